@@ -1,0 +1,200 @@
+/*
+ * tdks.h -- C ABI of the GB300 (sm_103a) library for real-time TDKS propagation
+ * with higher-order spectral finite elements (Kanungo & Gavini, arXiv 1810.13130).
+ *
+ * The method (paper Sec. III-VI):
+ *   * orbitals are expanded in C0 Lagrange elements on hexahedra whose nodes are
+ *     the Gauss-Lobatto-Legendre (GLL) points (Eq. 13, Sec. VI.A), with zero
+ *     Dirichlet values on the domain boundary;
+ *   * the overlap M is integrated with the GLL rule on those nodes, so it is
+ *     diagonal; every other integral uses the Gauss rule with nq = p+1 points per
+ *     direction (Sec. VI.A);
+ *   * the semi-discrete system i M psi' = H psi (Eqs. 14-15) is written in the
+ *     Loewdin basis psibar = M^1/2 psi, i psibar' = Hbar psibar,
+ *     Hbar = M^-1/2 H M^-1/2 (Eq. 21);
+ *   * one time step is the second-order Magnus propagator with the midpoint rule,
+ *     psibar^n = exp(-i dt Hbar[rho(t_{n-1} + dt/2)]) psibar^{n-1} (Eqs. 25-26),
+ *     the midpoint Hamiltonian coming from a predictor-corrector (Sec. VI.B);
+ *   * the exponential acts through adaptive Lanczos (Eqs. 36-38).
+ *
+ * Conventions for every entry point:
+ *   * Buffers suffixed _dev are device pointers owned by the caller; _host are host
+ *     pointers.  Complex vectors are interleaved (re, im) doubles.
+ *   * An orbital block psi is [n_orb][n_int] complex values: the Loewdin
+ *     coefficients psibar at the interior nodes, ordered x fastest, then y, then z.
+ *     Interior node (I, J, K), 1 <= I <= nx*p - 1 etc., has index
+ *     (I-1) + (nx*p-1) * ((J-1) + (ny*p-1) * (K-1)).
+ *   * Quadrature-point fields (potentials, densities) are [n_elem][nq^3] doubles,
+ *     element e = ex + nx*(ey + ny*ez), point q = qx + nq*(qy + nq*qz), Gauss
+ *     points ascending within each element.
+ *   * All work is ordered on the context's CUDA stream.  Calls that return host
+ *     values synchronize that stream; the others are asynchronous.
+ *   * Every call returns a tdks_status; nothing aborts or traps.  On failure,
+ *     tdks_last_error() describes the cause.  Device-side loops (Krylov, CG) are
+ *     bounded by iteration caps and report TDKS_ERR_NOT_CONVERGED.
+ */
+#ifndef TDKS_H
+#define TDKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdks_ctx tdks_ctx;
+
+typedef enum {
+  TDKS_OK = 0,
+  TDKS_ERR_ARG = -1,            /* invalid argument or descriptor            */
+  TDKS_ERR_CUDA = -2,           /* a CUDA runtime call failed                */
+  TDKS_ERR_NOMEM = -3,          /* device allocation failed                  */
+  TDKS_ERR_NOT_CONVERGED = -4,  /* Krylov sub-step or CG cap reached          */
+  TDKS_ERR_TIMEOUT = -5,        /* reserved for bounded device-side waits    */
+  TDKS_ERR_NAN = -6             /* a non-finite value reached a reduction     */
+} tdks_status;
+
+/* Arithmetic of the cell-level contractions in apply_H.  Vectors, Lanczos
+ * recurrence, small exponential, Poisson, density and dipole are always FP64. */
+typedef enum {
+  TDKS_FP64 = 0,   /* double contractions                                  */
+  TDKS_FP32 = 1    /* float contractions with float accumulation, FP64 I/O  */
+} tdks_prec;
+
+typedef enum {
+  TDKS_NUC_NONE = 0,
+  TDKS_NUC_SOFT = 1,       /* -Z / sqrt(r^2 + a2),  nuc_param = a2          */
+  TDKS_NUC_ERF = 2,        /* -Z erf(r / rc) / r,    nuc_param = rc          */
+  TDKS_NUC_BARE = 3,       /* -Z / r                                          */
+  TDKS_NUC_HARMONIC = 4    /* omega^2 |r - R_0|^2 / 2, nuc_param = omega      */
+} tdks_nuc_kind;
+
+/* Tensor-product hexahedral mesh: element breakpoints per axis (host arrays of
+ * length n+1, strictly increasing), polynomial degree 1 <= p <= 8, nq Gauss
+ * points per direction (0 selects p+1, the only value the GPU path accepts). */
+typedef struct {
+  int nx, ny, nz;
+  const double* X;
+  const double* Y;
+  const double* Z;
+  int p;
+  int nq;
+} tdks_mesh_desc;
+
+/* The electronic system: n_orb orbitals with occupations occ (host, length n_orb;
+ * 2.0 for doubly occupied), n_nuc nuclei at R (host, [n_nuc][3]) with charges Z,
+ * the nuclear potential form, and switches for the Hartree and LDA terms. */
+typedef struct {
+  int n_orb;
+  const double* occ;
+  int n_nuc;
+  const double* R;
+  const double* Z;
+  int nuc_kind;
+  double nuc_param;
+  int hartree;
+  int xc;
+} tdks_system_desc;
+
+/* Per-step statistics returned by tdks_magnus_step. */
+typedef struct {
+  int k_half_max;      /* largest Krylov dimension in the dt/2 predictor exp   */
+  int k_full_max;      /* largest Krylov dimension in the dt corrector exp     */
+  int64_t applies;     /* orbital-vector Hbar applications in this step        */
+  int substeps;        /* extra Krylov sub-steps taken (0 when none needed)    */
+  int cg_iters[3];     /* Poisson CG iterations: half-step, full-step, unused  */
+  double dipole[3];    /* dipole int r rho(t_n) dr                             */
+} tdks_stats;
+
+/* Create a context: builds the GLL/Gauss tables, the diagonal overlap (as 1-D
+ * factors), the nuclear potential at the Gauss points and the work buffers.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: TDKS_ERR_ARG for a malformed descriptor, TDKS_ERR_NOMEM, TDKS_ERR_CUDA. */
+tdks_status tdks_create(const tdks_mesh_desc* mesh, const tdks_system_desc* sys,
+                        void* stream, tdks_ctx** out);
+tdks_status tdks_destroy(tdks_ctx* ctx);
+tdks_status tdks_set_stream(tdks_ctx* ctx, void* stream);
+
+/* Sizes: interior nodes, elements, Gauss points per element. */
+tdks_status tdks_sizes(const tdks_ctx* ctx, int64_t* n_int, int64_t* n_elem, int* nq3);
+
+/* CG stopping rule for the Poisson solves: ||r|| <= tol ||b||, at most maxit. */
+tdks_status tdks_set_cg(tdks_ctx* ctx, double tol, int maxit);
+
+/* Copy the total Kohn-Sham potential V_KS at the Gauss points ([n_elem][nq^3],
+ * device) into the context; tdks_apply_H and tdks_expm act with it. */
+tdks_status tdks_set_potential(tdks_ctx* ctx, const double* v_q_dev);
+
+/* Copy the nuclear potential V_N at the Gauss points into v_q_dev. */
+tdks_status tdks_nuclear_potential(tdks_ctx* ctx, double* v_q_dev);
+
+/* out = Hbar psi for n_orb orbitals (Eqs. 15, 21): matrix-free, element by
+ * element: Loewdin scale and gather, interpolation to the Gauss points, the
+ * kinetic form 1/2 int grad N . grad N and the potential form int V N N, and the
+ * scatter-add with the Loewdin scale.  psi_dev and out_dev must not overlap. */
+tdks_status tdks_apply_H(tdks_ctx* ctx, const double* psi_dev, double* out_dev,
+                         int n_orb, int prec);
+
+/* rho(x_q) = sum_a occ_a |psi_a(x_q)|^2 with psi = M^-1/2 psibar (Eq. 2). */
+tdks_status tdks_density(tdks_ctx* ctx, const double* psi_dev, int n_orb, double* rho_q_dev);
+
+/* Dipole int r rho(r) dr by the Gauss rule (Sec. V, Eq. 30); synchronizes. */
+tdks_status tdks_dipole(tdks_ctx* ctx, const double* rho_q_dev, double d_host[3]);
+
+/* Hartree potential at the Gauss points: K phi = 4 pi c (Eq. 19), zero Dirichlet
+ * boundary, Jacobi PCG warm-started from the previous solution kept in the
+ * context.  iters_host receives the iteration count (may be NULL); synchronizes. */
+tdks_status tdks_hartree(tdks_ctx* ctx, const double* rho_q_dev, double* vh_q_dev,
+                         int* iters_host);
+
+/* LDA exchange-correlation potential v_xc(rho) at the Gauss points (Sec. II:
+ * Ceperley-Alder data, Perdew-Zunger 1981 unpolarized fit; 0 below rho = 1e-14). */
+tdks_status tdks_xc(tdks_ctx* ctx, const double* rho_q_dev, double* vxc_q_dev);
+
+/* psi_out = exp(-i tau Hbar) psi_in by adaptive Lanczos (Eqs. 36-38) with the
+ * potential last set by tdks_set_potential.  Stops each orbital when
+ * tau beta_k ||psi|| |[exp(-i tau T_k) e_1]_k| <= tol; at k_max (<= 128) without
+ * convergence it takes exact sub-steps tau_rem / 2^m.  psi_out may equal psi_in.
+ * k_used_host (may be NULL): [n_orb] sum of Krylov dimensions over sub-steps.
+ * Synchronizes. */
+tdks_status tdks_expm(tdks_ctx* ctx, const double* psi_in_dev, double* psi_out_dev,
+                      int n_orb, double tau, double tol, int k_max, int prec,
+                      int* k_used_host);
+
+/* Delta kick psibar_j <- exp(-i kappa dir . x_j) psibar_j at every interior node. */
+tdks_status tdks_kick(tdks_ctx* ctx, double* psi_dev, int n_orb, double kappa,
+                      const double dir[3]);
+
+/* Start a propagation from psi: V_HXC(t_0) from its density, history
+ * V_HXC(t_{-1}) := V_HXC(t_0).  d_host (may be NULL) receives the dipole. */
+tdks_status tdks_init_propagation(tdks_ctx* ctx, const double* psi_dev, int n_orb,
+                                  double d_host[3]);
+
+/* One predictor-corrector Magnus step (Eqs. 25-26, Sec. VI.B) in place:
+ *   V_pred = V_N + 1.25 V_HXC^{n-1} - 0.25 V_HXC^{n-2} - E_quarter . r
+ *   psi_half = exp(-i dt/2 Hbar[V_pred]) psi
+ *   V_mid = V_N + V_HXC[rho(psi_half)] - E_half . r
+ *   psi <- exp(-i dt Hbar[V_mid]) psi;  V_HXC^n from rho(psi)
+ * E_quarter, E_half: host 3-vectors, the field at t_{n-1} + dt/4 and + dt/2.
+ * stats (may be NULL) is filled; synchronizes. */
+tdks_status tdks_magnus_step(tdks_ctx* ctx, double* psi_dev, int n_orb, double dt,
+                             const double E_quarter[3], const double E_half[3],
+                             double tol, int k_max, int prec, tdks_stats* stats);
+
+/* End-to-end call with host buffers: copies psi_host_in to the device, runs
+ * tdks_init_propagation when init != 0, then n_steps Magnus steps with the field
+ * samples E_host ([n_steps][6]: E at t+dt/4 then at t+dt/2), writes the dipoles
+ * ([n_steps][3]) and copies the final orbitals to psi_host_out.  Uses a device
+ * orbital buffer owned by the context. */
+tdks_status tdks_propagate_host(tdks_ctx* ctx, const double* psi_host_in,
+                                double* psi_host_out, int n_orb, int init, int n_steps,
+                                double dt, const double* E_host, double tol, int k_max,
+                                int prec, double* dipole_host);
+
+const char* tdks_last_error(const tdks_ctx* ctx);
+const char* tdks_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDKS_H */

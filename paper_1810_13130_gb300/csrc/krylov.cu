@@ -1,0 +1,501 @@
+// Adaptive Lanczos approximation of exp(-i tau Hbar) psibar (Sec. VI.B, Eqs. 36-38).
+//
+// All orbitals of the block run the recurrence together, each with its own
+// tridiagonal T, stopping index and sub-steps:
+//   q_0 = psi / ||psi||;  w = Hbar q_j;  alpha_j = Re(q_j^H w)
+//   w -= alpha_j q_j + beta_{j-1} q_{j-1};  beta_j = ||w||;  q_{j+1} = w / beta_j
+//   y = exp(-i tau T_{j+1}) e_1,  eps = tau beta_j ||psi|| |y_j|,  stop at eps <= tol
+//   psi_out = ||psi|| sum_j y_j q_j
+// Basis vectors are stored unnormalized (V_j) with q_j = s_j V_j, and s_j is
+// folded into the next apply's gather.  alpha_j comes out of the apply kernel
+// as sum_e u_e^H H_e u_e (element partial sums), beta_j from the update kernel.
+//
+// The small exponential exp(-i tau T) e_1 of the real symmetric tridiagonal T
+// is evaluated on the device by the Chebyshev (Jacobi-Anger) expansion
+//   exp(-i tau x) = e^{-i tau c} sum_n (2 - delta_n0) (-i)^n J_n(tau R) T_n((x - c)/R)
+// on the Gershgorin interval [c - R, c + R] of T, with the Bessel values J_n
+// from Miller's backward recurrence normalized by J_0 + 2 sum J_2k = 1.  It
+// replaces the eigendecomposition of T (either is allowed by the paper, Eq. 37);
+// its truncation error is below 1e-16.
+//
+// With a cap k_max the unconverged basis serves the largest sub-step
+// tau_rem / 2^m whose estimate meets the tolerance, and the recurrence restarts.
+#include <cmath>
+
+#include "elements.cuh"
+#include "tdks_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBlocks = 608;
+constexpr int kBessMax = 3072;
+
+__device__ __forceinline__ double block_reduce_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ double sum_fixed(const double* part, int n, double* red) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+__global__ void k_kry_init(KryOrb* kry, int n_orb, double tau) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_orb) return;
+  KryOrb& K = kry[o];
+  K.t_rem = tau;
+  K.tau_sub = 0.0;
+  K.status = KRY_ACTIVE;
+  K.k = 0;
+  K.k_total = 0;
+  K.nsub = 0;
+  K.applies = 0;
+  K.pad = 0;
+}
+
+__global__ void k_norm_part(const double2* v, int64_t stride, long long n, const KryOrb* kry,
+                            double* part, int64_t pstride) {
+  __shared__ double red[kThreads / 32];
+  const int o = blockIdx.y;
+  double acc = 0.0;
+  if (kry[o].status == KRY_ACTIVE) {
+    const double2* p = v + (long long)o * stride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double2 a = p[i];
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+    }
+  }
+  const double s = block_reduce_sum(acc, red);
+  if (threadIdx.x == 0) part[(long long)o * pstride + blockIdx.x] = s;
+}
+
+__global__ void k_kry_start(KryOrb* kry, const double* part, int64_t pstride, int nb) {
+  __shared__ double red[kThreads / 32];
+  const int o = blockIdx.x;
+  KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  const double s = sum_fixed(part + (long long)o * pstride, nb, red);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(s);
+    K.nrm = nrm;
+    K.k = 0;
+    if (!isfinite(nrm)) {
+      K.status = KRY_FAILED;
+    } else if (nrm == 0.0) {
+      K.status = KRY_CONVERGED;   // exp of the zero vector: recombination writes zeros
+      K.tau_sub = K.t_rem;
+    } else {
+      K.s[0] = 1.0 / nrm;
+    }
+  }
+}
+
+// w = V_{j+1} - alpha_j s_j V_j - beta_{j-1} s_{j-1} V_{j-1} (in place), partial ||w||^2
+__global__ void k_kry_update(int j, long long n, double2* Vn, int64_t sn, const double2* Vj,
+                             int64_t sj, const double2* Vm, int64_t sm, KryOrb* kry,
+                             const double* apart, int64_t apstride, int napart, double* npart,
+                             int64_t npstride) {
+  __shared__ double red[kThreads / 32];
+  const int o = blockIdx.y;
+  KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  const double alpha = sum_fixed(apart + (long long)o * apstride, napart, red);
+  if (blockIdx.x == 0 && threadIdx.x == 0) K.alpha[j] = alpha;
+  const double a = alpha * K.s[j];
+  const double b = (j > 0) ? K.beta[j - 1] * K.s[j - 1] : 0.0;
+  double2* w = Vn + (long long)o * sn;
+  const double2* x = Vj + (long long)o * sj;
+  const double2* y = (j > 0) ? Vm + (long long)o * sm : nullptr;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 v = w[i];
+    const double2 u = x[i];
+    v.x = fma(-a, u.x, v.x);
+    v.y = fma(-a, u.y, v.y);
+    if (y) {
+      const double2 t = y[i];
+      v.x = fma(-b, t.x, v.x);
+      v.y = fma(-b, t.y, v.y);
+    }
+    w[i] = v;
+    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+  }
+  const double s = block_reduce_sum(acc, red);
+  if (threadIdx.x == 0) npart[(long long)o * npstride + blockIdx.x] = s;
+}
+
+// ---- small exponential on one warp -----------------------------------------
+struct ChebWork {
+  double J[kBessMax + 1];
+  double a[TDKS_KMAX], b[TDKS_KMAX];
+  double v0[TDKS_KMAX], v1[TDKS_KMAX], v2[TDKS_KMAX];
+  double yr[TDKS_KMAX], yi[TDKS_KMAX];
+  double scal[4];
+};
+
+__device__ __forceinline__ double warp_min(double v) {
+  for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+// y = exp(-i tau T) e_1 into W.yr/W.yi[0..m-1] (T from W.a, W.b); false if the
+// expansion would need more than kBessMax terms.  Called by a full warp.
+__device__ bool cheb_exp(int m, double tau, ChebWork& W) {
+  const int lane = threadIdx.x & 31;
+  if (m == 1) {
+    if (lane == 0) {
+      double sn, cs;
+      sincos(tau * W.a[0], &sn, &cs);
+      W.yr[0] = cs;
+      W.yi[0] = -sn;
+    }
+    __syncwarp();
+    return true;
+  }
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = lane; i < m; i += 32) {
+    const double r = (i > 0 ? fabs(W.b[i - 1]) : 0.0) + (i < m - 1 ? fabs(W.b[i]) : 0.0);
+    lo = fmin(lo, W.a[i] - r);
+    hi = fmax(hi, W.a[i] + r);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  const double c = 0.5 * (hi + lo);
+  const double R = 0.5 * (hi - lo);
+  double sn, cs;
+  sincos(tau * c, &sn, &cs);
+  const double z = tau * R;
+  if (!(R > 1e-300) || !(z > 1e-280)) {
+    for (int i = lane; i < m; i += 32) {
+      W.yr[i] = (i == 0) ? cs : 0.0;
+      W.yi[i] = (i == 0) ? -sn : 0.0;
+    }
+    __syncwarp();
+    return true;
+  }
+  const int N = (int)ceil(z + 14.0 * cbrt(z) + 25.0);
+  if (N > kBessMax) return false;
+  if (lane == 0) {
+    // Miller: b_{n-1} = (2n/z) b_n - b_{n+1} from n = M down to 1
+    const int M = N + 20;
+    const double inv_z = 1.0 / z;
+    double bn1 = 0.0, bn = 1e-280, S = (M % 2 == 0) ? 2.0 * bn : 0.0;
+    for (int n = M; n >= 1; --n) {
+      const double bm = (2.0 * n * inv_z) * bn - bn1;
+      const int idx = n - 1;
+      if (idx <= N) W.J[idx] = bm;
+      S += (idx == 0) ? bm : ((idx % 2 == 0) ? 2.0 * bm : 0.0);
+      bn1 = bn;
+      bn = bm;
+      if (fabs(bn) > 1e250) {
+        bn *= 1e-250;
+        bn1 *= 1e-250;
+        S *= 1e-250;
+        for (int k = idx; k <= N && k <= M; ++k) W.J[k] *= 1e-250;
+      }
+    }
+    const double inv = 1.0 / S;
+    for (int k = 0; k <= N; ++k) W.J[k] *= inv;
+  }
+  __syncwarp();
+  const double invR = 1.0 / R;
+  // v0 = e_1, v1 = S e_1
+  for (int i = lane; i < m; i += 32) {
+    W.v0[i] = (i == 0) ? 1.0 : 0.0;
+    double t = (i == 0) ? (W.a[0] - c) : 0.0;
+    if (i == 1) t = W.b[0];
+    W.v1[i] = t * invR;
+  }
+  __syncwarp();
+  double accr[TDKS_KMAX / 32], acci[TDKS_KMAX / 32];
+  for (int r = 0; r < TDKS_KMAX / 32; ++r) {
+    const int i = lane + 32 * r;
+    accr[r] = (i < m) ? W.J[0] * W.v0[i] : 0.0;
+    acci[r] = (i < m) ? -2.0 * W.J[1] * W.v1[i] : 0.0;
+  }
+  double* vp = W.v0;
+  double* vc = W.v1;
+  double* vn = W.v2;
+  for (int n = 2; n <= N; ++n) {
+    for (int r = 0; r < TDKS_KMAX / 32; ++r) {
+      const int i = lane + 32 * r;
+      if (i < m) {
+        double t = (W.a[i] - c) * vc[i];
+        if (i > 0) t = fma(W.b[i - 1], vc[i - 1], t);
+        if (i < m - 1) t = fma(W.b[i], vc[i + 1], t);
+        vn[i] = fma(2.0 * invR, t, -vp[i]);
+      }
+    }
+    __syncwarp();
+    const double cf = 2.0 * W.J[n];
+    const int ph = n & 3;
+    for (int r = 0; r < TDKS_KMAX / 32; ++r) {
+      const int i = lane + 32 * r;
+      if (i < m) {
+        const double v = cf * vn[i];
+        if (ph == 0) accr[r] += v;
+        else if (ph == 1) acci[r] -= v;
+        else if (ph == 2) accr[r] -= v;
+        else acci[r] += v;
+      }
+    }
+    double* t = vp;
+    vp = vc;
+    vc = vn;
+    vn = t;
+    __syncwarp();
+  }
+  for (int r = 0; r < TDKS_KMAX / 32; ++r) {
+    const int i = lane + 32 * r;
+    if (i < m) {
+      // multiply by e^{-i tau c} = cs - i sn
+      W.yr[i] = accr[r] * cs + acci[r] * sn;
+      W.yi[i] = acci[r] * cs - accr[r] * sn;
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// One warp per orbital: beta_j, small exponential, a-posteriori estimate, decision.
+__global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double* npart,
+                          int64_t npstride, int nb) {
+  __shared__ ChebWork W;
+  const int o = blockIdx.x;
+  const int lane = threadIdx.x;
+  KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  double v = 0.0;
+  for (int k = lane; k < nb; k += 32) v += npart[(long long)o * npstride + k];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const double beta = sqrt(v);
+  const int m = j + 1;
+  for (int i = lane; i < m; i += 32) {
+    W.a[i] = K.alpha[i];
+    W.b[i] = (i < m - 1) ? K.beta[i] : 0.0;
+  }
+  __syncwarp();
+  int decision = 0;   // 0 continue, 1 converged, 2 sub-step, -1 failed
+  double tau_used = K.t_rem;
+  if (!isfinite(beta)) {
+    decision = -1;
+  } else {
+    const bool ok = cheb_exp(m, K.t_rem, W);
+    const double err = ok ? K.t_rem * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
+    if (ok && (err <= tol || beta == 0.0)) {
+      decision = 1;
+    } else if (m >= kmax) {
+      decision = -1;
+      for (int s = 1; s < 60; ++s) {
+        const double ts = ldexp(K.t_rem, -s);
+        const bool ok2 = cheb_exp(m, ts, W);
+        const double e2 = ok2 ? ts * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
+        if (ok2 && e2 <= tol) {
+          decision = 2;
+          tau_used = ts;
+          break;
+        }
+      }
+    }
+  }
+  for (int i = lane; i < m; i += 32) {
+    K.yre[i] = W.yr[i];
+    K.yim[i] = W.yi[i];
+  }
+  if (lane == 0) {
+    K.applies += 1;
+    K.beta[j] = beta;
+    K.k = m;
+    if (decision == 0) {
+      K.s[j + 1] = 1.0 / beta;
+    } else if (decision == 1) {
+      K.status = KRY_CONVERGED;
+      K.tau_sub = K.t_rem;
+    } else if (decision == 2) {
+      K.status = KRY_SUBSTEP;
+      K.tau_sub = tau_used;
+    } else {
+      K.status = KRY_FAILED;
+    }
+  }
+}
+
+// out = ||psi|| sum_j y_j s_j V_j
+__global__ void k_kry_recomb(long long n, double2* out, int64_t so, const double2* V0, int64_t s0,
+                             const double2* Vw, int64_t sw, int kmax, const KryOrb* kry) {
+  __shared__ double cr[TDKS_KMAX], ci[TDKS_KMAX];
+  const int o = blockIdx.y;
+  const KryOrb& K = kry[o];
+  const int st = K.status;
+  if (st != KRY_CONVERGED && st != KRY_SUBSTEP) return;
+  const int m = K.k;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double f = K.nrm * K.s[j];
+    cr[j] = f * K.yre[j];
+    ci[j] = f * K.yim[j];
+  }
+  __syncthreads();
+  const double2* v0 = V0 + (long long)o * s0;
+  const double2* vw = Vw + (long long)o * sw;
+  double2* dst = out + (long long)o * so;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
+      re = fma(cr[j], v.x, fma(-ci[j], v.y, re));
+      im = fma(cr[j], v.y, fma(ci[j], v.x, im));
+    }
+    dst[i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_kry_after(KryOrb* kry, int n_orb) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_orb) return;
+  KryOrb& K = kry[o];
+  if (K.status == KRY_CONVERGED || K.status == KRY_SUBSTEP) {
+    K.k_total += K.k;
+    K.nsub += 1;
+    if (K.k > K.pad) K.pad = K.k;       // largest dimension seen
+    if (K.status == KRY_CONVERGED) {
+      K.t_rem = 0.0;
+      K.status = KRY_DONE;
+    } else {
+      K.t_rem -= K.tau_sub;
+      K.status = (K.nsub >= TDKS_MAX_SUBSTEPS) ? KRY_FAILED : KRY_ACTIVE;
+    }
+  }
+}
+
+int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  return (int)(b < kBlocks ? (b < 1 ? 1 : b) : kBlocks);
+}
+
+}  // namespace
+
+tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb) {
+  // the buffer is sized at context creation for the system's orbital count
+  if (!c->d_part || per_orb > c->part_stride || n_orb > c->n_orb)
+    return tdks_fail(c, TDKS_ERR_ARG, "partial-sum buffer too small for this call");
+  return TDKS_OK;
+}
+
+static tdks_status ensure_krylov(tdks_ctx* c, int n_orb, int kmax) {
+  if (c->d_V && c->V_orb >= n_orb && c->V_kmax == kmax) return TDKS_OK;
+  if (c->d_V) cudaFree(c->d_V);
+  c->d_V = nullptr;
+  const size_t bytes = (size_t)n_orb * kmax * c->n_int * sizeof(double2);
+  if (cudaMalloc(&c->d_V, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return tdks_fail(c, TDKS_ERR_NOMEM, "Krylov basis (" + std::to_string(bytes >> 20) + " MiB)");
+  }
+  c->V_orb = n_orb;
+  c->V_kmax = kmax;
+  return TDKS_OK;
+}
+
+struct KrySummary {
+  int k, status, k_total, nsub, applies, kseen;
+};
+
+static tdks_status read_summary(tdks_ctx* c, int n_orb, KrySummary* h) {
+  TDKS_CU(c, cudaMemcpy2DAsync(h, sizeof(KrySummary), &c->d_kry[0].k, sizeof(KryOrb),
+                               sizeof(KrySummary), n_orb, cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CU(c, cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
+tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, double tau,
+                     double tol, int kmax, int prec, int* k_used, int* kmax_seen,
+                     int64_t* applies, int* nsub) {
+  if (kmax < 1 || kmax > TDKS_KMAX) return tdks_fail(c, TDKS_ERR_ARG, "k_max must be in [1, 128]");
+  if (n_orb < 1 || n_orb > c->n_orb) return tdks_fail(c, TDKS_ERR_ARG, "n_orb out of range");
+  const long long n = c->n_int;
+  const int bpc = hbar_blocks_per_color(c);
+  TDKS_TRY(ensure_part(c, n_orb, 8 * (int64_t)bpc));
+  TDKS_TRY(ensure_krylov(c, n_orb, kmax));
+  const int64_t ps = c->part_stride;
+  double* apart = c->d_part;
+  double* npart = c->d_part + (int64_t)c->n_orb * ps;
+  const int nb = grid_for(n);
+  const int64_t wsorb = (int64_t)kmax * n;   // stride between orbitals in the workspace
+  std::vector<KrySummary> h(n_orb);
+  k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb, tau);
+  TDKS_CU(c, cudaGetLastError());
+  const double2* cur = in;
+  for (int sub = 0; sub <= TDKS_MAX_SUBSTEPS; ++sub) {
+    k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(cur, n, n, c->d_kry, npart, ps);
+    k_kry_start<<<n_orb, kThreads, 0, c->stream>>>(c->d_kry, npart, ps, nb);
+    TDKS_CU(c, cudaGetLastError());
+    for (int j = 0; j < kmax; ++j) {
+      const double2* Vj = (j == 0) ? cur : c->d_V + (int64_t)(j - 1) * n;
+      const int64_t sj = (j == 0) ? n : wsorb;
+      const double2* Vm = (j == 1) ? cur : (j >= 2 ? c->d_V + (int64_t)(j - 2) * n : nullptr);
+      const int64_t sm = (j == 1) ? n : wsorb;
+      double2* Vn = c->d_V + (int64_t)j * n;
+      TDKS_CU(c, cudaMemset2DAsync(Vn, wsorb * sizeof(double2), 0, n * sizeof(double2), n_orb,
+                                   c->stream));
+      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, c->d_kry, j, apart, ps};
+      TDKS_TRY(launch_hbar_apply(c, a, prec));
+      k_kry_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(j, n, Vn, wsorb, Vj, sj, Vm, sm,
+                                                               c->d_kry, apart, ps, 8 * bpc, npart,
+                                                               ps);
+      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, c->d_kry, npart, ps, nb);
+      TDKS_CU(c, cudaGetLastError());
+      TDKS_TRY(read_summary(c, n_orb, h.data()));
+      bool any = false;
+      for (int o = 0; o < n_orb; ++o) any |= (h[o].status == KRY_ACTIVE);
+      if (!any) break;
+    }
+    k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, c->d_V, wsorb,
+                                                             kmax, c->d_kry);
+    k_kry_after<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb);
+    TDKS_CU(c, cudaGetLastError());
+    TDKS_TRY(read_summary(c, n_orb, h.data()));
+    bool any = false, failed = false;
+    for (int o = 0; o < n_orb; ++o) {
+      any |= (h[o].status == KRY_ACTIVE);
+      failed |= (h[o].status == KRY_FAILED);
+    }
+    if (failed)
+      return tdks_fail(c, TDKS_ERR_NOT_CONVERGED,
+                       "Lanczos: no admissible sub-step, sub-step cap or non-finite norm");
+    if (!any) break;
+    cur = out;
+  }
+  int64_t napp = 0;
+  int kseen = 0, ns = 0;
+  for (int o = 0; o < n_orb; ++o) {
+    if (k_used) k_used[o] = h[o].k_total;
+    napp += h[o].applies;
+    kseen = h[o].kseen > kseen ? h[o].kseen : kseen;
+    ns += h[o].nsub - 1;
+  }
+  if (kmax_seen) *kmax_seen = kseen;
+  if (applies) *applies = napp;
+  if (nsub) *nsub = ns;
+  return TDKS_OK;
+}

@@ -1,0 +1,188 @@
+// Internal declarations of the TDKS library (context, tables, launch helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tdks.h"
+
+#define TDKS_KMAX 128          // hard cap on the Krylov dimension per sub-step
+#define TDKS_MAX_P1 9          // p <= 8
+#define TDKS_MAX_SUBSTEPS 1000
+
+// Per-orbital Lanczos state, resident in device memory.
+struct KryOrb {
+  double nrm;                  // ||psi|| at the start of the current sub-step
+  double t_rem;                // time still to propagate
+  double tau_sub;              // time covered by the current sub-step's result
+  int k;                       // Krylov vectors built in the current sub-step
+  int status;                  // KRY_* below
+  int k_total;                 // sum of Krylov dimensions over sub-steps
+  int nsub;                    // sub-steps taken
+  int applies;                 // Hbar applications on this orbital
+  int pad;
+  double alpha[TDKS_KMAX];
+  double beta[TDKS_KMAX];
+  double s[TDKS_KMAX + 1];     // basis vector j is q_j = s[j] * V_j
+  double yre[TDKS_KMAX];
+  double yim[TDKS_KMAX];
+};
+
+enum { KRY_ACTIVE = 0, KRY_CONVERGED = 1, KRY_SUBSTEP = 2, KRY_DONE = 3, KRY_FAILED = -1 };
+
+// CG state, resident in device memory.
+struct CgState {
+  double bb;        // ||b||^2
+  double rz;        // r.z of the current iterate
+  double rr;        // ||r||^2
+  double alpha;
+  int iters;
+  int done;         // 1 when converged
+  int failed;
+  int pad;
+};
+
+// Geometry passed by value to the element kernels.
+struct Geom {
+  int nx, ny, nz, p;
+  int nix, niy, niz;           // interior nodes per axis
+  const double* brk[3];        // breakpoints per axis (n+1)
+  const double* s[3];          // 1-D factors of M^-1/2 per full node index
+  const double* gauss;         // Gauss points on [-1, 1] (P1)
+};
+
+struct tdks_ctx {
+  // mesh
+  int nx = 0, ny = 0, nz = 0, p = 0, P1 = 0, nq = 0;
+  int Nn[3] = {0, 0, 0}, Ni[3] = {0, 0, 0};
+  int64_t n_int = 0, n_elem = 0, nq3 = 0;
+  std::vector<double> brk[3];
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // system
+  int n_orb = 0;
+  std::vector<double> occ, R, Z;
+  int n_nuc = 0, nuc_kind = 0, hartree = 1, xc = 1;
+  double nuc_param = 0.0;
+  // device mesh data
+  double* d_brk[3] = {nullptr, nullptr, nullptr};
+  double* d_s[3] = {nullptr, nullptr, nullptr};          // M^-1/2 1-D factors
+  double* d_coord[3] = {nullptr, nullptr, nullptr};      // node coordinates
+  double* d_kd[3] = {nullptr, nullptr, nullptr};         // sum K1_aa / h  (Jacobi diagonal)
+  double* d_md[3] = {nullptr, nullptr, nullptr};         // sum h Mg_aa
+  double* d_tab = nullptr;     // double tables (layout in tables.cpp)
+  float* d_tabf = nullptr;     // float copy
+  double* d_occ = nullptr;
+  double* d_R = nullptr;
+  double* d_Z = nullptr;
+  // fields at the Gauss points
+  double *d_vks = nullptr, *d_vnuc = nullptr, *d_vhxc1 = nullptr, *d_vhxc2 = nullptr;
+  double *d_vtmp = nullptr, *d_rho = nullptr, *d_vh = nullptr;
+  // Poisson
+  double *d_phi = nullptr, *d_b = nullptr, *d_r = nullptr, *d_pv = nullptr, *d_Ap = nullptr;
+  CgState* d_cg = nullptr;
+  double cg_tol = 1e-12;
+  int cg_maxit = 5000;
+  // Krylov
+  double2* d_V = nullptr;      // [n_orb][kmax][n_int]
+  int V_orb = 0, V_kmax = 0;
+  KryOrb* d_kry = nullptr;
+  KryOrb* h_kry = nullptr;     // pinned mirror (status reads)
+  double2* d_psi_half = nullptr;
+  double2* d_psi_e2e = nullptr;
+  // reductions
+  double* d_part = nullptr;    // partial sums
+  int64_t part_stride = 0;     // per orbital
+  double* h_red = nullptr;     // pinned small host buffer
+  int* h_int = nullptr;
+  bool propagation_ready = false;
+  std::string err;
+};
+
+// ---------------------------------------------------------------- helpers
+tdks_status tdks_fail(tdks_ctx* c, tdks_status s, const std::string& msg);
+tdks_status tdks_cuda_check(tdks_ctx* c, cudaError_t e, const char* what);
+#define TDKS_CU(ctx, call)                                              \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return tdks_cuda_check((ctx), e_, #call);    \
+  } while (0)
+#define TDKS_TRY(call)                     \
+  do {                                     \
+    tdks_status s_ = (call);               \
+    if (s_ != TDKS_OK) return s_;          \
+  } while (0)
+
+Geom tdks_geom(const tdks_ctx* c);
+
+// tables.cpp: host construction of the 1-D tables (long double)
+struct Tables1D {
+  std::vector<double> xi, w;       // GLL nodes and weights (P1)
+  std::vector<double> eta, omega;  // Gauss points and weights (nq)
+  std::vector<double> B, D;        // [nq][P1] Lagrange values / derivatives at Gauss points
+  std::vector<double> Kq;          // [nq][nq] Dg^T diag(omega) Dg on Gauss-point Lagrange basis
+  std::vector<double> K1, Mg;      // [P1][P1] D^T W D and B^T W B
+};
+Tables1D tdks_build_tables(int p, int nq);
+
+#ifdef __CUDACC__
+#define TDKS_HD __host__ __device__
+#else
+#define TDKS_HD
+#endif
+
+// Device table layout (both double and float copies), offsets in elements.
+//   B [P1*P1] | Kq [P1*P1] | w [P1] | K1 [P1*P1] | Mg [P1*P1] | eta [P1]
+TDKS_HD inline int tab_off_B(int) { return 0; }
+TDKS_HD inline int tab_off_Kq(int P1) { return P1 * P1; }
+TDKS_HD inline int tab_off_w(int P1) { return 2 * P1 * P1; }
+TDKS_HD inline int tab_off_K1(int P1) { return 2 * P1 * P1 + P1; }
+TDKS_HD inline int tab_off_Mg(int P1) { return 3 * P1 * P1 + P1; }
+TDKS_HD inline int tab_off_eta(int P1) { return 4 * P1 * P1 + P1; }
+TDKS_HD inline int tab_size(int P1) { return 4 * P1 * P1 + 2 * P1; }
+
+// ---------------------------------------------------------------- launchers
+// element kernels (elements.cu)
+struct ApplyArgs {
+  const double2* in_base;
+  int64_t in_stride;
+  double2* out_base;
+  int64_t out_stride;
+  int n_orb;
+  const KryOrb* kry;          // optional: scale s[kj], skip non-active orbitals
+  int kj;
+  double* part;               // optional: per-block partial of Re(u^H Hu) per orbital
+  int64_t part_stride;
+};
+tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec);
+tdks_status launch_stiffness(tdks_ctx* c, const double* in, double* out, double* part,
+                             const CgState* cg);
+tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, double scale);
+tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q);
+tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q);
+int hbar_blocks_per_color(const tdks_ctx* c);
+int stiff_blocks_per_color(const tdks_ctx* c);
+
+// fields.cu
+tdks_status launch_nuclear(tdks_ctx* c);
+tdks_status launch_xc(tdks_ctx* c, const double* rho, double* vxc);
+tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3]);
+tdks_status launch_kick(tdks_ctx* c, double2* psi, int n_orb, double kappa, const double dir[3]);
+// v_out = vn + a1*h1 + a2*h2 + h3 - E.x_q   (h2/h3 may be null)
+tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double a1,
+                           const double* h1, double a2, const double* h2,
+                           const double* h3, const double E[3]);
+
+// poisson.cu
+tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters);
+
+// krylov.cu
+tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, double tau,
+                     double tol, int kmax, int prec, int* k_used, int* kmax_seen,
+                     int64_t* applies, int* nsub);
+
+// reduction helper used by several files
+tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the C ABI in include/tdks.h (argument marshalling only).
+
+Device buffers are torch tensors on the current CUDA device: orbital blocks are
+complex128 [n_orb, n_int], quadrature fields float64 [n_elem, nq^3].  Work runs
+on torch's current stream.  If libtdks.so is missing this module raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdks.so")
+
+FP64, FP32 = 0, 1
+NUC_KIND = {"none": 0, "soft": 1, "erf": 2, "bare": 3, "harmonic": 4}
+_dp = C.POINTER(C.c_double)
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("X", _dp), ("Y", _dp),
+                ("Z", _dp), ("p", C.c_int), ("nq", C.c_int)]
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("n_orb", C.c_int), ("occ", _dp), ("n_nuc", C.c_int), ("R", _dp), ("Z", _dp),
+                ("nuc_kind", C.c_int), ("nuc_param", C.c_double), ("hartree", C.c_int),
+                ("xc", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("k_half_max", C.c_int), ("k_full_max", C.c_int), ("applies", C.c_int64),
+                ("substeps", C.c_int), ("cg_iters", C.c_int * 3), ("dipole", C.c_double * 3)]
+
+    def as_dict(self):
+        return {"k_half_max": self.k_half_max, "k_full_max": self.k_full_max,
+                "applies": int(self.applies), "substeps": self.substeps,
+                "cg_iters": list(self.cg_iters)[:2], "dipole": list(self.dipole)}
+
+
+class TDKSError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libtdks.so (built by paper_1810_13130_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise TDKSError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    v, p, i, d, i64 = C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "tdks_create": [C.POINTER(MeshDesc), C.POINTER(SystemDesc), v, C.POINTER(C.c_void_p)],
+        "tdks_destroy": [v],
+        "tdks_set_stream": [v, v],
+        "tdks_sizes": [v, C.POINTER(i64), C.POINTER(i64), C.POINTER(i)],
+        "tdks_set_cg": [v, d, i],
+        "tdks_set_potential": [v, p],
+        "tdks_nuclear_potential": [v, p],
+        "tdks_apply_H": [v, p, p, i, i],
+        "tdks_density": [v, p, i, p],
+        "tdks_dipole": [v, p, _dp],
+        "tdks_hartree": [v, p, p, C.POINTER(i)],
+        "tdks_xc": [v, p, p],
+        "tdks_expm": [v, p, p, i, d, d, i, i, C.POINTER(i)],
+        "tdks_kick": [v, p, i, d, _dp],
+        "tdks_init_propagation": [v, p, i, _dp],
+        "tdks_magnus_step": [v, p, i, d, _dp, _dp, d, i, i, C.POINTER(Stats)],
+        "tdks_propagate_host": [v, p, p, i, i, i, d, p, d, i, i, p],
+        "tdks_last_error": [v],
+        "tdks_status_string": [i],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name in ("tdks_last_error", "tdks_status_string") else C.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list:
+    return [n for n in ("tdks_create", "tdks_destroy", "tdks_set_stream", "tdks_sizes",
+                        "tdks_set_cg", "tdks_set_potential", "tdks_nuclear_potential",
+                        "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
+                        "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
+                        "tdks_propagate_host", "tdks_last_error", "tdks_status_string")]
+
+
+def _darr(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t: torch.Tensor, dtype, what: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TDKSError(f"{what}: expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TDKSError(f"{what}: expected a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """Owns a tdks_ctx.  Mirrors tdks_create / tdks_destroy; methods mirror the
+    remaining entry points (tdks_<name>)."""
+
+    def __init__(self, X, Y, Z, p: int, n_orb: int, occ, atom_R=None, atom_Z=None,
+                 nuc_kind: str = "none", nuc_param: float = 0.0, hartree: bool = True,
+                 xc: bool = True, nq: int = 0):
+        L = lib()
+        self._keep = [_darr(X), _darr(Y), _darr(Z), _darr(occ)]
+        R = _darr(atom_R if atom_R is not None else np.zeros((0, 3))).reshape(-1)
+        Zc = _darr(atom_Z if atom_Z is not None else np.zeros(0))
+        self._keep += [R, Zc]
+        m = MeshDesc(len(X) - 1, len(Y) - 1, len(Z) - 1, _ptr(self._keep[0]), _ptr(self._keep[1]),
+                     _ptr(self._keep[2]), int(p), int(nq))
+        s = SystemDesc(int(n_orb), _ptr(self._keep[3]), len(Zc), _ptr(R) if len(Zc) else None,
+                       _ptr(Zc) if len(Zc) else None, NUC_KIND[nuc_kind], float(nuc_param),
+                       int(bool(hartree)), int(bool(xc)))
+        h = C.c_void_p()
+        st = L.tdks_create(C.byref(m), C.byref(s), C.c_void_p(_stream()), C.byref(h))
+        if st != 0:
+            raise TDKSError(f"tdks_create: {L.tdks_status_string(st).decode()}")
+        self.h = h
+        self.n_orb = int(n_orb)
+        ni, ne, nq3 = C.c_int64(), C.c_int64(), C.c_int()
+        L.tdks_sizes(h, C.byref(ni), C.byref(ne), C.byref(nq3))
+        self.n_int, self.n_elem, self.nq3 = ni.value, ne.value, nq3.value
+
+    @classmethod
+    def from_config(cls, cfg):
+        return cls(cfg.X, cfg.Y, cfg.Z, cfg.p, cfg.n_orb, cfg.occ, cfg.atom_R, cfg.atom_Z,
+                   cfg.nuc_kind, cfg.nuc_param, cfg.hartree, cfg.xc, cfg.nq)
+
+    def _check(self, st: int, name: str):
+        if st != 0:
+            L = lib()
+            raise TDKSError(f"{name}: {L.tdks_status_string(st).decode()}: "
+                            f"{L.tdks_last_error(self.h).decode()}")
+
+    def _sync_stream(self):
+        lib().tdks_set_stream(self.h, C.c_void_p(_stream()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tdks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- allocation helpers (torch owns the memory) -------------------------
+    def empty_orbitals(self, n_orb: Optional[int] = None) -> torch.Tensor:
+        return torch.empty((n_orb or self.n_orb, self.n_int), dtype=torch.complex128, device="cuda")
+
+    def empty_field(self) -> torch.Tensor:
+        return torch.empty((self.n_elem, self.nq3), dtype=torch.float64, device="cuda")
+
+    # -- entry points ---------------------------------------------------------
+    def set_cg(self, tol: float, maxit: int = 5000):
+        self._check(lib().tdks_set_cg(self.h, tol, maxit), "tdks_set_cg")
+
+    def set_potential(self, v_q: torch.Tensor):
+        self._sync_stream()
+        self._check(lib().tdks_set_potential(self.h, _dev(v_q, torch.float64, "v_q")),
+                    "tdks_set_potential")
+
+    def nuclear_potential(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.empty_field() if out is None else out
+        self._sync_stream()
+        self._check(lib().tdks_nuclear_potential(self.h, _dev(out, torch.float64, "out")),
+                    "tdks_nuclear_potential")
+        return out
+
+    def apply_H(self, psi: torch.Tensor, out: Optional[torch.Tensor] = None, prec: int = FP64):
+        out = torch.empty_like(psi) if out is None else out
+        self._sync_stream()
+        self._check(lib().tdks_apply_H(self.h, _dev(psi, torch.complex128, "psi"),
+                                       _dev(out, torch.complex128, "out"), psi.shape[0], prec),
+                    "tdks_apply_H")
+        return out
+
+    def density(self, psi: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.empty_field() if out is None else out
+        self._sync_stream()
+        self._check(lib().tdks_density(self.h, _dev(psi, torch.complex128, "psi"), psi.shape[0],
+                                       _dev(out, torch.float64, "rho")), "tdks_density")
+        return out
+
+    def dipole(self, rho: torch.Tensor) -> np.ndarray:
+        d = np.zeros(3)
+        self._sync_stream()
+        self._check(lib().tdks_dipole(self.h, _dev(rho, torch.float64, "rho"), _ptr(d)),
+                    "tdks_dipole")
+        return d
+
+    def hartree(self, rho: torch.Tensor, out: Optional[torch.Tensor] = None):
+        out = self.empty_field() if out is None else out
+        it = C.c_int()
+        self._sync_stream()
+        self._check(lib().tdks_hartree(self.h, _dev(rho, torch.float64, "rho"),
+                                       _dev(out, torch.float64, "vh"), C.byref(it)), "tdks_hartree")
+        return out, it.value
+
+    def xc(self, rho: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.empty_field() if out is None else out
+        self._sync_stream()
+        self._check(lib().tdks_xc(self.h, _dev(rho, torch.float64, "rho"),
+                                  _dev(out, torch.float64, "vxc")), "tdks_xc")
+        return out
+
+    def expm(self, psi: torch.Tensor, tau: float, tol: float = 1e-10, k_max: int = 64,
+             prec: int = FP64, out: Optional[torch.Tensor] = None):
+        out = torch.empty_like(psi) if out is None else out
+        k = (C.c_int * psi.shape[0])()
+        self._sync_stream()
+        self._check(lib().tdks_expm(self.h, _dev(psi, torch.complex128, "psi"),
+                                    _dev(out, torch.complex128, "out"), psi.shape[0], tau, tol,
+                                    k_max, prec, k), "tdks_expm")
+        return out, list(k)
+
+    def kick(self, psi: torch.Tensor, kappa: float, direction: Sequence[float]):
+        d = _darr(direction)
+        self._sync_stream()
+        self._check(lib().tdks_kick(self.h, _dev(psi, torch.complex128, "psi"), psi.shape[0],
+                                    kappa, _ptr(d)), "tdks_kick")
+        return psi
+
+    def init_propagation(self, psi: torch.Tensor) -> np.ndarray:
+        d = np.zeros(3)
+        self._sync_stream()
+        self._check(lib().tdks_init_propagation(self.h, _dev(psi, torch.complex128, "psi"),
+                                                psi.shape[0], _ptr(d)), "tdks_init_propagation")
+        return d
+
+    def magnus_step(self, psi: torch.Tensor, dt: float, E_quarter=(0, 0, 0), E_half=(0, 0, 0),
+                    tol: float = 1e-10, k_max: int = 64, prec: int = FP64) -> dict:
+        eq, eh = _darr(E_quarter), _darr(E_half)
+        st = Stats()
+        self._sync_stream()
+        self._check(lib().tdks_magnus_step(self.h, _dev(psi, torch.complex128, "psi"),
+                                           psi.shape[0], dt, _ptr(eq), _ptr(eh), tol, k_max, prec,
+                                           C.byref(st)), "tdks_magnus_step")
+        return st.as_dict()
+
+    def propagate_host(self, psi_in: torch.Tensor, psi_out: torch.Tensor, n_steps: int,
+                       dt: float, E: Optional[np.ndarray] = None, init: bool = True,
+                       tol: float = 1e-10, k_max: int = 64, prec: int = FP64) -> np.ndarray:
+        """Host-buffer path: psi_in/psi_out are CPU complex128 tensors (pinned for speed)."""
+        for t, nm in ((psi_in, "psi_in"), (psi_out, "psi_out")):
+            if t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+                raise TDKSError(f"{nm}: expected a contiguous CPU complex128 tensor")
+        Eh = None if E is None else _darr(E).reshape(n_steps, 6)
+        dip = np.zeros((max(n_steps, 1), 3))
+        self._sync_stream()
+        self._check(lib().tdks_propagate_host(
+            self.h, psi_in.data_ptr(), psi_out.data_ptr(), psi_in.shape[0], int(init), n_steps, dt,
+            None if Eh is None else Eh.ctypes.data, tol, k_max, prec, dip.ctypes.data),
+            "tdks_propagate_host")
+        return dip[:n_steps]

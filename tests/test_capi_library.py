@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point declared in include/tdks.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tdks.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:tdks_status|const char\*)\s+(tdks_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1810_13130_gb300.build import build
+    return build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("tdks_create", "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree",
+              "tdks_expm", "tdks_magnus_step", "tdks_set_potential", "tdks_propagate_host"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    from paper_1810_13130_gb300 import tdks
+    assert set(_declared()) <= set(tdks.exported_symbols())
+    lib = tdks.lib()
+    assert lib.tdks_status_string(-4).decode() == "not converged"
+
+
+def test_create_rejects_bad_descriptors_without_gpu(libpath):
+    """Argument validation happens before any CUDA call."""
+    from paper_1810_13130_gb300 import tdks
+    L = tdks.lib()
+    import numpy as np
+    X = np.array([0.0, 1.0, 0.5])          # not increasing
+    occ = np.array([2.0])
+    m = tdks.MeshDesc(2, 2, 2, X.ctypes.data_as(tdks._dp), X.ctypes.data_as(tdks._dp),
+                      X.ctypes.data_as(tdks._dp), 3, 0)
+    s = tdks.SystemDesc(1, occ.ctypes.data_as(tdks._dp), 0, None, None, 0, 0.0, 1, 1)
+    h = ctypes.c_void_p()
+    assert L.tdks_create(ctypes.byref(m), ctypes.byref(s), None, ctypes.byref(h)) == -1
+    Xg = np.array([0.0, 1.0, 2.0])
+    m = tdks.MeshDesc(2, 2, 2, Xg.ctypes.data_as(tdks._dp), Xg.ctypes.data_as(tdks._dp),
+                      Xg.ctypes.data_as(tdks._dp), 9, 0)          # p = 9 unsupported
+    assert L.tdks_create(ctypes.byref(m), ctypes.byref(s), None, ctypes.byref(h)) == -1
+    m = tdks.MeshDesc(2, 2, 2, Xg.ctypes.data_as(tdks._dp), Xg.ctypes.data_as(tdks._dp),
+                      Xg.ctypes.data_as(tdks._dp), 3, 5)          # nq != p+1
+    assert L.tdks_create(ctypes.byref(m), ctypes.byref(s), None, ctypes.byref(h)) == -1
