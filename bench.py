@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the Magnus-Lanczos TDKS step on one GB300 (or N replicas).
+
+A step is one predictor-corrector second-order Magnus step (two adaptive
+Lanczos exponentials, two Poisson solves, densities, LDA, dipole) of the
+16-orbital molecule workload: [-16,16]^3 bohr, 16^3 hexahedra, p = 6
+(857,375 interior DoF), 8 erf-pseudopotential atoms, Hartree + LDA, dt = 0.1,
+Krylov tolerance 1e-10.  Metric: orbital-steps/s (value) and H-psi GDoF/s.
+
+  python bench.py [--gpus N --steps K --warmup W] [--prec fp64|fp32]
+  python bench.py --impl reference ...    # the CPU oracle on a bounded sample
+
+Inputs are synthetic and resident in HBM before the timed region; the working
+set (Krylov basis, 16 x 64 x 857k complex128 = 14 GB) is far larger than L2.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("orbital-steps/s & HΨ GDoF/s, mixed/batched vs FP64 on 1 GB300 at dipole "
+          "err≤1e-6")
+FP64_PEAK_TFLOPS = 1.25          # GB300 dense FP64 (profiling recipe table); probe: 1.256
+FP32_PEAK_TFLOPS = 73.5          # measured FFMA rate of this machine's GB300 (FMA probe)
+PROFILE = os.path.join(ROOT, "profiles", "hbar_fp64_molecule.txt")
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# the oracle on a bounded sample (CPU baseline and reference arm)
+# ----------------------------------------------------------------------------
+ORACLE_SAMPLE_DESC = (
+    "oracle (numpy, 1 thread) on the same workload: per measured step, 8 Lanczos iterations "
+    "of the dt/2 exponential and the density of one of the 16 orbitals; the Krylov "
+    "dimensions k_half, k_full of both exponentials come from a set-up run, so one "
+    "orbital-step costs (k_half + k_full) H-applications + one density.  The two Poisson "
+    "solves per step are not included, so the oracle rate is an upper bound.")
+
+
+def oracle_sample_main(spec: str):
+    """Runs in a fresh single-threaded interpreter; prints one JSON line per step."""
+    import numpy as np
+    import synth
+    from oracle import hamiltonian as ham
+    from oracle import xc
+    from oracle.lanczos import expm_lanczos
+    from oracle.mesh import Mesh
+    from oracle.propagate import Propagator, kick
+    a = json.loads(spec)
+    cfg = synth.config2()
+    mesh = Mesh.from_config(cfg)
+    prop = Propagator.from_config(cfg, mesh)
+    psi = synth.smooth_orbitals(tuple(mesh.Ni), cfg.n_orb, seed=a["seed"])
+    psi = kick(mesh, psi, cfg.kick, cfg.kick_dir)
+    rho = ham.density(mesh, psi, cfg.occ)
+    v = prop.v_nuc + xc.v_xc(rho)
+    f = lambda x: ham.apply_H(mesh, v, x)
+    # set-up: Krylov dimensions of both exponentials for orbital 0
+    _, i_half = expm_lanczos(f, psi[:1], 0.5 * cfg.dt, cfg.tol, cfg.k_max)
+    _, i_full = expm_lanczos(f, psi[:1], cfg.dt, cfg.tol, cfg.k_max)
+    k_half, k_full = sum(i_half["k"][0]), sum(i_full["k"][0])
+    print(json.dumps({"setup": True, "k_half": k_half, "k_full": k_full}), flush=True)
+    for s in range(a["steps"]):
+        o = s % cfg.n_orb
+        t0 = time.perf_counter()
+        expm_lanczos(f, psi[o:o + 1], 0.5 * cfg.dt, cfg.tol, cfg.k_max, k_fixed=8)
+        t1 = time.perf_counter()
+        ham.density(mesh, psi[o:o + 1], cfg.occ[o:o + 1])
+        t2 = time.perf_counter()
+        kh = 8
+        t_apply = (t1 - t0) / kh
+        t_orb_step = (k_half + k_full) * t_apply + (t2 - t1)
+        print(json.dumps({"step": s, "t_sample": t2 - t0, "orbital_steps_per_s": 1.0 / t_orb_step,
+                          "k_half": kh}), flush=True)
+
+
+def run_oracle_sample(steps: int, seed: int = 1):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               PYTHONPATH=ROOT)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample",
+           json.dumps({"steps": steps, "seed": seed})]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def reference_arm(args, rank: int):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    recs = run_oracle_sample(args.warmup + args.steps)
+    wall = time.perf_counter() - t0
+    timed = [r for r in recs if "step" in r][args.warmup:]
+    rates = [r["orbital_steps_per_s"] for r in timed]
+    value = statistics.mean(rates)
+    tsum = sum(r["t_sample"] for r in timed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "orbital-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * 16 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "molecule_erf8_16x16x16_p6 (857,375 DoF, 16 orbitals, dt 0.1)",
+                   "sample": "one orbital per step"},
+        "cpu_baseline": {"value": value, "unit": "orbital-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": ORACLE_SAMPLE_DESC, "timed_sample_s": tsum,
+                         "wall_s_incl_setup": wall},
+        "e2e": {"value": value, "unit": "orbital-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={SMI_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def profile_traffic(prec: str):
+    """dram bytes per Hbar launch from the committed ncu summary, if the kernel
+    source has not changed since the capture."""
+    if prec != "fp64" or not os.path.exists(PROFILE):
+        return None
+    src = open(os.path.join(ROOT, "paper_1810_13130_gb300", "csrc", "elements.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("elements_cu_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_color_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import synth
+    from paper_1810_13130_gb300 import tdks
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = tdks.FP64 if args.prec == "fp64" else tdks.FP32
+    cfg = synth.config2()
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_cg(1e-10)
+    psi0 = synth.smooth_orbitals(tuple(n * cfg.p - 1 for n in (cfg.nx, cfg.ny, cfg.nz)),
+                                 cfg.n_orb, seed=1)
+    psi = torch.from_numpy(psi0).cuda()
+    ctx.kick(psi, cfg.kick, cfg.kick_dir)
+    ctx.init_propagation(psi)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ctx.magnus_step(psi, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=prec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.get_counters(reset=True)
+    ctx.set_timing(True)
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    cnt = ctx.get_counters(reset=True)
+    ctx.set_timing(False)
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    n_int = ctx.n_int
+    applies = sum(s["applies"] for s in stats)
+    value = world * cfg.n_orb * args.steps / t
+    hpsi = world * n_int * applies / t / 1e9
+    # roofline of the dominant kernel (Hbar colour launches, timed inside the region)
+    P1 = cfg.p + 1
+    flops_unit = 36 * P1 ** 4 + 24 * P1 ** 3
+    apply_s = cnt["apply_ms"] * 1e-3
+    achieved_tf = cnt["apply_elem_orb"] * flops_unit / apply_s / 1e12 if apply_s > 0 else None
+    peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
+    bytes_apply_unit = None
+    launches_per_apply = 8
+    n_apply_calls = cnt["apply_launches"] / launches_per_apply
+    avg_launch_ms = cnt["apply_ms"] / max(cnt["apply_launches"], 1)
+    hbm_bytes = applies * n_int * 32.0 + n_apply_calls * ctx.n_elem * P1 ** 3 * 8.0
+    traffic = profile_traffic(args.prec)
+    roofline = {"bound": "alu", "kernel": f"k_hbar<P1={P1},{args.prec}> (8 parity-colour launches per apply)",
+                "achieved": achieved_tf, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved_tf / peak) if achieved_tf else None, "traffic": traffic,
+                "peak_source": ("nominal FP64 rate of the profiling recipe (DFMA probe 1.256)"
+                                if args.prec == "fp64" else "measured FFMA probe"),
+                "flops_per_elem_orbital": flops_unit,
+                "avg_launch_ms": avg_launch_ms, "apply_share_of_step": apply_s / t,
+                "hbm_GBps_algorithmic": hbm_bytes / apply_s / 1e9 if apply_s > 0 else None,
+                "hbm_frac_of_measured_6793": (hbm_bytes / apply_s / 1e9 / 6793.1) if apply_s > 0 else None}
+    line = {"metric": METRIC, "value": value, "unit": "orbital-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "molecule_erf8_16x16x16_p6: [-16,16]^3 bohr, 16^3 hexahedra, "
+                                   "p=6, 857,375 DoF, 16 orbitals, 8 erf atoms, Hartree+LDA, "
+                                   "kick 1e-3 x, dt 0.1, Krylov tol 1e-10",
+                       "contractions": args.prec, "parallelism": f"replicas x{world}",
+                       "l2": "working set > L2 (Krylov basis 14 GB, orbitals 219 MB)"},
+            "hpsi_gdofs": hpsi, "applies_per_step": applies / args.steps,
+            "krylov": {"k_half_max": max(s["k_half_max"] for s in stats),
+                       "k_full_max": max(s["k_full_max"] for s in stats),
+                       "substeps": sum(s["substeps"] for s in stats),
+                       "cg_iters_per_solve": statistics.mean(c for s in stats for c in s["cg_iters"])},
+            "roofline": roofline, "gpu_launches": cnt["launches"], "clocks": clk.summary()}
+    # end to end through the public C-ABI with host buffers (pinned), every step:
+    # H2D of the orbitals + field, the step, D2H of the orbitals + dipole
+    if args.e2e_steps > 0:
+        hin = psi.cpu().pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        E = np.zeros(6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.propagate_host(hin, hout, 1, cfg.dt, E, init=False, tol=cfg.tol, k_max=cfg.k_max,
+                               prec=prec)
+            hin, hout = hout, hin
+        te = time.perf_counter() - t0
+        nb = cfg.n_orb * n_int * 16
+        line["e2e"] = {"value": world * cfg.n_orb * args.e2e_steps / te, "unit": "orbital-steps/s",
+                       "h2d_bytes_per_step": nb + 48, "d2h_bytes_per_step": nb + 24,
+                       "steps": args.e2e_steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        recs = run_oracle_sample(1)
+        st = [r for r in recs if "step" in r]
+        line["cpu_baseline"] = {"value": st[0]["orbital_steps_per_s"], "unit": "orbital-steps/s",
+                                "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_DESC,
+                                "timed_sample_s": st[0]["t_sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.oracle_sample is not None:
+        oracle_sample_main(args.oracle_sample)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -191,6 +191,21 @@ tdks_status tdks_propagate_host(tdks_ctx* ctx, const double* psi_host_in,
                                 double dt, const double* E_host, double tol, int k_max,
                                 int prec, double* dipole_host);
 
+/* Work counters of a context (for benchmarking): kernel launches issued, Hbar
+ * colour launches, element-orbital applications, and -- when timing is on --
+ * the summed device time of the Hbar applications inside tdks_expm measured
+ * with CUDA events on the context's stream.  reset != 0 zeroes them after
+ * reading.  out may be NULL (reset only). */
+typedef struct {
+  int64_t launches;
+  int64_t apply_launches;
+  int64_t apply_elem_orb;
+  double apply_ms;
+  int64_t cg_iters;
+} tdks_counters;
+tdks_status tdks_set_timing(tdks_ctx* ctx, int on);
+tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);
+
 const char* tdks_last_error(const tdks_ctx* ctx);
 const char* tdks_status_string(int status);
 

@@ -90,6 +90,8 @@ void free_ctx(tdks_ctx* c) {
   cudaFree(c->d_psi_e2e);
   cudaFree(c->d_part);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->ev[0]) cudaEventDestroy(c->ev[0]);
+  if (c->ev[1]) cudaEventDestroy(c->ev[1]);
   delete c;
 }
 
@@ -314,6 +316,7 @@ tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb,
   if (prec != TDKS_FP64 && prec != TDKS_FP32) return tdks_fail(c, TDKS_ERR_ARG, "precision");
   TDKS_CU(c, cudaMemsetAsync(out, 0, (size_t)n_orb * c->n_int * sizeof(double2), c->stream));
   ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0};
+  c->n_apply_units += (int64_t)n_orb * c->n_elem;
   return launch_hbar_apply(c, a, prec);
 }
 
@@ -430,6 +433,28 @@ tdks_status tdks_propagate_host(tdks_ctx* c, const double* psi_in, double* psi_o
   }
   TDKS_CU(c, cudaMemcpyAsync(psi_out, c->d_psi_e2e, vb, cudaMemcpyDeviceToHost, c->stream));
   TDKS_CU(c, cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_timing(tdks_ctx* c, int on) {
+  if (!c) return TDKS_ERR_ARG;
+  c->timing = on != 0;
+  return TDKS_OK;
+}
+
+tdks_status tdks_get_counters(tdks_ctx* c, tdks_counters* out, int reset) {
+  if (!c) return TDKS_ERR_ARG;
+  if (out) {
+    out->launches = c->n_launch;
+    out->apply_launches = c->n_apply_launch;
+    out->apply_elem_orb = c->n_apply_units;
+    out->apply_ms = c->apply_ms;
+    out->cg_iters = c->n_cg;
+  }
+  if (reset) {
+    c->n_launch = c->n_apply_launch = c->n_apply_units = c->n_cg = 0;
+    c->apply_ms = 0.0;
+  }
   return TDKS_OK;
 }
 

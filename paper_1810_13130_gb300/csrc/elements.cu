@@ -442,6 +442,8 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   for (int color = 0; color < 8; ++color) {
     k_hbar<P1, T><<<grid, block, smem, c->stream>>>(g, tab, c->d_vks, a, color, opc, color * bpc);
   }
+  c->n_launch += 8;
+  c->n_apply_launch += 8;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -456,6 +458,7 @@ tdks_status stiff_t(tdks_ctx* c, const double* in, double* out, double* part, co
   const Geom g = tdks_geom(c);
   for (int color = 0; color < 8; ++color)
     k_stiff<P1><<<grid, block, smem, c->stream>>>(g, c->d_tab, in, out, part, color * bpc, cg, color);
+  c->n_launch += 8;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -469,6 +472,7 @@ tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale) {
   const Geom g = tdks_geom(c);
   for (int color = 0; color < 8; ++color)
     k_load<P1><<<grid, block, smem, c->stream>>>(g, c->d_tab, fq, out, scale, color);
+  c->n_launch += 8;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -480,6 +484,7 @@ tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq) {
   TDKS_CU(c, set_smem(k_interp<P1>, smem));
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
   k_interp<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, nodal, fq);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -492,6 +497,7 @@ tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho) {
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
   k_density<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, psi, c->n_int, n_orb,
                                                  c->d_occ, rho);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }

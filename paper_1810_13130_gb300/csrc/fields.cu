@@ -176,6 +176,7 @@ tdks_status launch_nuclear(tdks_ctx* c) {
   k_nuclear<<<vec_grid(n), kVecThreads, 0, c->stream>>>(
       tdks_geom(c), c->d_tab + tab_off_eta(c->P1), c->P1, n, c->nuc_kind, c->nuc_param, c->n_nuc,
       c->d_R, c->d_Z, c->d_vnuc);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -183,6 +184,7 @@ tdks_status launch_nuclear(tdks_ctx* c) {
 tdks_status launch_xc(tdks_ctx* c, const double* rho, double* vxc) {
   const long long n = c->n_elem * c->nq3;
   k_xc<<<vec_grid(n), kVecThreads, 0, c->stream>>>(rho, vxc, n);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -196,6 +198,7 @@ tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double 
   k_combine<<<vec_grid(n), kVecThreads, 0, c->stream>>>(tdks_geom(c), c->d_tab + tab_off_eta(c->P1),
                                                         c->P1, n, v_out, vn, a1, h1, a2, h2, h3,
                                                         e[0], e[1], e[2]);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -208,6 +211,7 @@ tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3]) {
   k_dipole_part<<<nb, kVecThreads, 0, c->stream>>>(tdks_geom(c), c->d_tab + tab_off_eta(c->P1),
                                                    c->d_tab + tab_off_w(c->P1), c->P1, n, rho, part);
   k_sum_parts3<<<1, 32, 0, c->stream>>>(part, nb, out);
+  c->n_launch += 2;
   TDKS_CU(c, cudaGetLastError());
   TDKS_CU(c, cudaMemcpyAsync(c->h_red, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TDKS_CU(c, cudaStreamSynchronize(c->stream));
@@ -219,6 +223,7 @@ tdks_status launch_kick(tdks_ctx* c, double2* psi, int n_orb, double kappa, cons
   k_kick<<<vec_grid(c->n_int), kVecThreads, 0, c->stream>>>(
       c->d_coord[0], c->d_coord[1], c->d_coord[2], c->Ni[0], c->Ni[1], c->n_int, n_orb, psi, kappa,
       dir[0], dir[1], dir[2]);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }

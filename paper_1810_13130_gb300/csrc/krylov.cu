@@ -444,11 +444,18 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
   const int64_t wsorb = (int64_t)kmax * n;   // stride between orbitals in the workspace
   std::vector<KrySummary> h(n_orb);
   k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb, tau);
+  c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
+  if (c->timing && !c->ev[0]) {
+    TDKS_CU(c, cudaEventCreate(&c->ev[0]));
+    TDKS_CU(c, cudaEventCreate(&c->ev[1]));
+  }
+  int n_active = n_orb;
   const double2* cur = in;
   for (int sub = 0; sub <= TDKS_MAX_SUBSTEPS; ++sub) {
     k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(cur, n, n, c->d_kry, npart, ps);
     k_kry_start<<<n_orb, kThreads, 0, c->stream>>>(c->d_kry, npart, ps, nb);
+    c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
     for (int j = 0; j < kmax; ++j) {
       const double2* Vj = (j == 0) ? cur : c->d_V + (int64_t)(j - 1) * n;
@@ -459,20 +466,30 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
       TDKS_CU(c, cudaMemset2DAsync(Vn, wsorb * sizeof(double2), 0, n * sizeof(double2), n_orb,
                                    c->stream));
       ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, c->d_kry, j, apart, ps};
+      if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[0], c->stream));
       TDKS_TRY(launch_hbar_apply(c, a, prec));
+      if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
+      c->n_apply_units += (int64_t)n_active * c->n_elem;
       k_kry_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(j, n, Vn, wsorb, Vj, sj, Vm, sm,
                                                                c->d_kry, apart, ps, 8 * bpc, npart,
                                                                ps);
       k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, c->d_kry, npart, ps, nb);
+      c->n_launch += 2;
       TDKS_CU(c, cudaGetLastError());
       TDKS_TRY(read_summary(c, n_orb, h.data()));
-      bool any = false;
-      for (int o = 0; o < n_orb; ++o) any |= (h[o].status == KRY_ACTIVE);
-      if (!any) break;
+      if (c->timing) {
+        float ms = 0.f;
+        TDKS_CU(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->apply_ms += ms;
+      }
+      n_active = 0;
+      for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
+      if (!n_active) break;
     }
     k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, c->d_V, wsorb,
                                                              kmax, c->d_kry);
     k_kry_after<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb);
+    c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
     TDKS_TRY(read_summary(c, n_orb, h.data()));
     bool any = false, failed = false;
@@ -484,6 +501,8 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
       return tdks_fail(c, TDKS_ERR_NOT_CONVERGED,
                        "Lanczos: no admissible sub-step, sub-step cap or non-finite norm");
     if (!any) break;
+    n_active = 0;
+    for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
     cur = out;
   }
   int64_t napp = 0;

@@ -181,6 +181,7 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
   TDKS_TRY(launch_stiffness(c, c->d_phi, c->d_Ap, nullptr, nullptr));
   k_cg_init<<<nb, kThreads, 0, c->stream>>>(n, c->d_b, c->d_Ap, c->d_r, c->d_pv, dg, part_vec);
   k_cg_init_fin<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, c->d_cg);
+  c->n_launch += 2;
   TDKS_CU(c, cudaGetLastError());
   int it = 0;
   CgState host{};
@@ -192,6 +193,7 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
                                                   c->d_Ap, dg, part_vec, c->d_cg);
       k_cg_fin<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, c->cg_maxit, c->d_cg);
       k_cg_dir<<<nb, kThreads, 0, c->stream>>>(n, c->d_r, c->d_pv, dg, c->d_cg);
+      c->n_launch += 3;
     }
     TDKS_CU(c, cudaGetLastError());
     it += kPoll;
@@ -201,6 +203,7 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
     if (it > c->cg_maxit + kPoll) break;
   }
   if (iters) *iters = host.iters;
+  c->n_cg += host.iters;
   if (host.failed == 3) {
     TDKS_CU(c, cudaMemsetAsync(c->d_phi, 0, n * sizeof(double), c->stream));
     host.failed = 0;

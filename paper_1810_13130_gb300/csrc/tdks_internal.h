@@ -99,6 +99,11 @@ struct tdks_ctx {
   double* h_red = nullptr;     // pinned small host buffer
   int* h_int = nullptr;
   bool propagation_ready = false;
+  // counters
+  int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0;
+  double apply_ms = 0.0;
+  bool timing = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   std::string err;
 };
 

@@ -43,6 +43,11 @@ class Stats(C.Structure):
                 "cg_iters": list(self.cg_iters)[:2], "dipole": list(self.dipole)}
 
 
+class Counters(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("apply_launches", C.c_int64),
+                ("apply_elem_orb", C.c_int64), ("apply_ms", C.c_double), ("cg_iters", C.c_int64)]
+
+
 class TDKSError(RuntimeError):
     pass
 
@@ -77,6 +82,8 @@ def lib():
         "tdks_init_propagation": [v, p, i, _dp],
         "tdks_magnus_step": [v, p, i, d, _dp, _dp, d, i, i, C.POINTER(Stats)],
         "tdks_propagate_host": [v, p, p, i, i, i, d, p, d, i, i, p],
+        "tdks_set_timing": [v, i],
+        "tdks_get_counters": [v, C.POINTER(Counters), i],
         "tdks_last_error": [v],
         "tdks_status_string": [i],
     }
@@ -93,7 +100,8 @@ def exported_symbols() -> list:
                         "tdks_set_cg", "tdks_set_potential", "tdks_nuclear_potential",
                         "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
-                        "tdks_propagate_host", "tdks_last_error", "tdks_status_string")]
+                        "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
+                        "tdks_last_error", "tdks_status_string")]
 
 
 def _darr(a) -> np.ndarray:
@@ -167,6 +175,15 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_timing(self, on: bool):
+        self._check(lib().tdks_set_timing(self.h, int(bool(on))), "tdks_set_timing")
+
+    def get_counters(self, reset: bool = False) -> dict:
+        c = Counters()
+        self._check(lib().tdks_get_counters(self.h, C.byref(c), int(bool(reset))),
+                    "tdks_get_counters")
+        return {k: getattr(c, k) for k, _ in Counters._fields_}
 
     # -- allocation helpers (torch owns the memory) -------------------------
     def empty_orbitals(self, n_orb: Optional[int] = None) -> torch.Tensor:
