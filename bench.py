@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time standalone Hbar applications (16 orbitals) instead of steps")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -246,11 +248,13 @@ def ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")
         ev0.record(stream)
         for _ in range(args.steps):
             stats.append(step())
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     t = ev0.elapsed_time(ev1) * 1e-3
@@ -330,6 +334,44 @@ def ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+def apply_only(args, local_rank: int):
+    """Standalone Hbar psi on the benchmark workload (16 orbitals, random
+    orbitals, V = V_N): the kernel in isolation, for the roofline and ncu."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1810_13130_gb300 import tdks
+    torch.cuda.set_device(local_rank)
+    prec = tdks.FP64 if args.prec == "fp64" else tdks.FP32
+    cfg = synth.config2()
+    ctx = tdks.Context.from_config(cfg)
+    psi = torch.from_numpy(synth.random_psi(cfg.n_orb, ctx.n_int, seed=3)).cuda()
+    ctx.set_potential(ctx.nuclear_potential())
+    out = torch.empty_like(psi)
+    for _ in range(args.warmup):
+        ctx.apply_H(psi, out, prec)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            ctx.apply_H(psi, out, prec)
+        ev1.record()
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) * 1e-3 / args.steps
+    P1 = cfg.p + 1
+    units = cfg.n_orb * ctx.n_elem
+    flops = units * (36 * P1 ** 4 + 24 * P1 ** 3)
+    byts = cfg.n_orb * ctx.n_int * 32.0 + ctx.n_elem * P1 ** 3 * 8.0   # read psi, write Hpsi, V
+    peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
+    print(json.dumps({"mode": "apply_only", "prec": args.prec, "ms_per_apply": t * 1e3,
+                      "hpsi_gdofs": cfg.n_orb * ctx.n_int / t / 1e9,
+                      "tflops": flops / t / 1e12, "frac_alu": flops / t / 1e12 / peak,
+                      "hbm_GBps": byts / t / 1e9, "frac_hbm": byts / t / 1e9 / 6793.1,
+                      "clocks": clk.summary()}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.oracle_sample is not None:
@@ -340,6 +382,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank)
+        return
+    if args.apply_only:
+        apply_only(args, local_rank)
         return
     ours(args, rank, world, local_rank)
 

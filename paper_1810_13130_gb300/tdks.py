@@ -86,6 +86,7 @@ def lib():
         "tdks_get_counters": [v, C.POINTER(Counters), i],
         "tdks_last_error": [v],
         "tdks_status_string": [i],
+        "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -101,7 +102,7 @@ def exported_symbols() -> list:
                         "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
-                        "tdks_last_error", "tdks_status_string")]
+                        "tdks_dipole_noalloc", "tdks_last_error", "tdks_status_string")]
 
 
 def _darr(a) -> np.ndarray:
@@ -122,6 +123,19 @@ def _dev(t: torch.Tensor, dtype, what: str) -> int:
 
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
+
+
+def dipole_noalloc(rho: torch.Tensor, X, Y, Z, p: int) -> np.ndarray:
+    """tdks_dipole_noalloc: the dipole without a context and without any device
+    allocation (fixed scratch inside the library); calls must not overlap."""
+    Xa, Ya, Za = _darr(X), _darr(Y), _darr(Z)
+    d = np.zeros(3)
+    st = lib().tdks_dipole_noalloc(_dev(rho, torch.float64, "rho"), len(Xa) - 1, len(Ya) - 1,
+                                   len(Za) - 1, _ptr(Xa), _ptr(Ya), _ptr(Za), int(p),
+                                   C.c_void_p(_stream()), _ptr(d))
+    if st != 0:
+        raise TDKSError(f"tdks_dipole_noalloc: {lib().tdks_status_string(st).decode()}")
+    return d
 
 
 class Context:
