@@ -118,8 +118,13 @@ tdks_status tdks_set_stream(tdks_ctx* ctx, void* stream);
 /* Sizes: interior nodes, elements, Gauss points per element. */
 tdks_status tdks_sizes(const tdks_ctx* ctx, int64_t* n_int, int64_t* n_elem, int* nq3);
 
-/* CG stopping rule for the Poisson solves: ||r|| <= tol ||b||, at most maxit. */
-tdks_status tdks_set_cg(tdks_ctx* ctx, double tol, int maxit);
+/* Poisson CG: stopping rule ||r|| <= tol ||b|| (at most maxit iterations) and
+ * preconditioner.  TDKS_PRECOND_FDM (default) is the fast-diagonalization inverse
+ * of the separable stiffness of an axis-aligned tensor mesh (exact up to rounding:
+ * CG stops after one or two iterations); it is unavailable when an axis has more
+ * than 1024 interior nodes (TDKS_ERR_ARG), where Jacobi is the default. */
+typedef enum { TDKS_PRECOND_FDM = 0, TDKS_PRECOND_JACOBI = 1 } tdks_precond;
+tdks_status tdks_set_cg(tdks_ctx* ctx, double tol, int maxit, int precond);
 
 /* Copy the total Kohn-Sham potential V_KS at the Gauss points ([n_elem][nq^3],
  * device) into the context; tdks_apply_H and tdks_expm act with it. */
@@ -142,8 +147,9 @@ tdks_status tdks_density(tdks_ctx* ctx, const double* psi_dev, int n_orb, double
 tdks_status tdks_dipole(tdks_ctx* ctx, const double* rho_q_dev, double d_host[3]);
 
 /* Hartree potential at the Gauss points: K phi = 4 pi c (Eq. 19), zero Dirichlet
- * boundary, Jacobi PCG warm-started from the previous solution kept in the
- * context.  iters_host receives the iteration count (may be NULL); synchronizes. */
+ * boundary, preconditioned CG (see tdks_set_cg) warm-started from the previous
+ * solution kept in the context.  iters_host receives the iteration count (may be
+ * NULL); synchronizes. */
 tdks_status tdks_hartree(tdks_ctx* ctx, const double* rho_q_dev, double* vh_q_dev,
                          int* iters_host);
 

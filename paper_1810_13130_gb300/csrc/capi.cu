@@ -89,6 +89,14 @@ void free_ctx(tdks_ctx* c) {
   cudaFree(c->d_psi_half);
   cudaFree(c->d_psi_e2e);
   cudaFree(c->d_part);
+  cudaFree(c->d_z);
+  cudaFree(c->d_t1);
+  cudaFree(c->d_t2);
+  cudaFree(c->d_invdiag);
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(c->d_fdmS[d]);
+    cudaFree(c->d_fdmL[d]);
+  }
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->ev[0]) cudaEventDestroy(c->ev[0]);
   if (c->ev[1]) cudaEventDestroy(c->ev[1]);
@@ -258,6 +266,7 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
   if ((st = dalloc(c, &c->d_part, (size_t)(2 * (c->n_orb + 2) * c->part_stride + 8192))) != TDKS_OK)
     return fail(st);
   if (cudaMallocHost((void**)&c->h_red, 64 * sizeof(double)) != cudaSuccess) return fail(TDKS_ERR_NOMEM);
+  if ((st = poisson_setup(c, t)) != TDKS_OK) return fail(st);
   if ((st = launch_nuclear(c)) != TDKS_OK) return fail(st);
   if (cudaMemcpyAsync(c->d_vks, c->d_vnuc, nf * sizeof(double), cudaMemcpyDeviceToDevice,
                       c->stream) != cudaSuccess)
@@ -288,11 +297,16 @@ tdks_status tdks_sizes(const tdks_ctx* c, int64_t* n_int, int64_t* n_elem, int* 
   return TDKS_OK;
 }
 
-tdks_status tdks_set_cg(tdks_ctx* c, double tol, int maxit) {
+tdks_status tdks_set_cg(tdks_ctx* c, double tol, int maxit, int precond) {
   if (!c) return TDKS_ERR_ARG;
   if (!(tol > 0) || maxit < 1) return tdks_fail(c, TDKS_ERR_ARG, "cg tol > 0, maxit >= 1");
+  if (precond != TDKS_PRECOND_FDM && precond != TDKS_PRECOND_JACOBI)
+    return tdks_fail(c, TDKS_ERR_ARG, "unknown preconditioner");
+  if (precond == TDKS_PRECOND_FDM && !c->fdm_ok)
+    return tdks_fail(c, TDKS_ERR_ARG, "fast diagonalization unavailable for this mesh");
   c->cg_tol = tol;
   c->cg_maxit = maxit;
+  c->cg_precond = precond;
   return TDKS_OK;
 }
 

@@ -38,11 +38,11 @@ struct CgState {
   double bb;        // ||b||^2
   double rz;        // r.z of the current iterate
   double rr;        // ||r||^2
-  double alpha;
+  double alpha;     // CG step length; carries beta between the last two kernels
   int iters;
   int done;         // 1 when converged
   int failed;
-  int pad;
+  int first;        // 1 until the first search direction is set
 };
 
 // Geometry passed by value to the element kernels.
@@ -86,6 +86,11 @@ struct tdks_ctx {
   CgState* d_cg = nullptr;
   double cg_tol = 1e-12;
   int cg_maxit = 5000;
+  int cg_precond = 0;          // 0: fast diagonalization (exact for these meshes), 1: Jacobi
+  bool fdm_ok = false;
+  double* d_fdmS[3] = {nullptr, nullptr, nullptr};    // per-axis eigenvectors [i][mode]
+  double* d_fdmL[3] = {nullptr, nullptr, nullptr};    // per-axis eigenvalues
+  double *d_z = nullptr, *d_t1 = nullptr, *d_t2 = nullptr, *d_invdiag = nullptr;
   // Krylov
   double2* d_V = nullptr;      // [n_orb][kmax][n_int]
   int V_orb = 0, V_kmax = 0;
@@ -132,6 +137,9 @@ struct Tables1D {
   std::vector<double> K1, Mg;      // [P1][P1] D^T W D and B^T W B
 };
 Tables1D tdks_build_tables(int p, int nq);
+// fdm.cpp: generalized eigenpairs (1-D stiffness, 1-D Gauss mass) of one axis
+void tdks_fdm_axis(const Tables1D& t, int p, const double* br, int n_el, std::vector<double>& S,
+                   std::vector<double>& lam);
 
 #ifdef __CUDACC__
 #define TDKS_HD __host__ __device__
@@ -183,6 +191,7 @@ tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double 
 
 // poisson.cu
 tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters);
+tdks_status poisson_setup(tdks_ctx* c, const Tables1D& t);
 
 // krylov.cu
 tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, double tau,

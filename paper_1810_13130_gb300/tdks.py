@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdks.so")
 
 FP64, FP32 = 0, 1
+PRECOND_FDM, PRECOND_JACOBI = 0, 1
 NUC_KIND = {"none": 0, "soft": 1, "erf": 2, "bare": 3, "harmonic": 4}
 _dp = C.POINTER(C.c_double)
 
@@ -69,7 +70,7 @@ def lib():
         "tdks_destroy": [v],
         "tdks_set_stream": [v, v],
         "tdks_sizes": [v, C.POINTER(i64), C.POINTER(i64), C.POINTER(i)],
-        "tdks_set_cg": [v, d, i],
+        "tdks_set_cg": [v, d, i, i],
         "tdks_set_potential": [v, p],
         "tdks_nuclear_potential": [v, p],
         "tdks_apply_H": [v, p, p, i, i],
@@ -207,8 +208,8 @@ class Context:
         return torch.empty((self.n_elem, self.nq3), dtype=torch.float64, device="cuda")
 
     # -- entry points ---------------------------------------------------------
-    def set_cg(self, tol: float, maxit: int = 5000):
-        self._check(lib().tdks_set_cg(self.h, tol, maxit), "tdks_set_cg")
+    def set_cg(self, tol: float, maxit: int = 5000, precond: int = PRECOND_FDM):
+        self._check(lib().tdks_set_cg(self.h, tol, maxit, precond), "tdks_set_cg")
 
     def set_potential(self, v_q: torch.Tensor):
         self._sync_stream()

@@ -104,11 +104,13 @@ def test_apply_H_fp32_error_vs_fp64_oracle():
     assert 1e-9 < err < 1e-5
 
 
-def test_fields_match_oracle():
+@pytest.mark.parametrize("precond", [0, 1])
+def test_fields_match_oracle(precond):
     cfg = synth.small_config(3, 2, 2, p=4, n_orb=2, nuc_kind="erf", graded=True)
     cfg.nuc_param = 0.8
     m = Mesh.from_config(cfg)
     ctx = _ctx(cfg)
+    ctx.set_cg(1e-13, 5000, precond)
     vn_ref = nuclear_potential(m, "erf", cfg.atom_R, cfg.atom_Z, 0.8)
     assert _rel(ctx.nuclear_potential().cpu().numpy(), vn_ref) < 1e-14
     psi = synth.smooth_orbitals(tuple(m.Ni), 2, seed=3)
@@ -120,6 +122,26 @@ def test_fields_match_oracle():
     vh, it = ctx.hartree(rho)
     vh_ref, _, _ = poisson.hartree(m, rho_ref, tol=1e-13)
     assert _rel(vh.cpu().numpy(), vh_ref) < 1e-10 and it > 0
+    if precond == 0:
+        assert it <= 3          # exact inverse: one or two iterations
+    # warm start: the same right-hand side again converges at once
+    vh2, it2 = ctx.hartree(rho)
+    assert it2 <= 1 and _rel(vh2.cpu().numpy(), vh_ref) < 1e-10
+
+
+def test_hartree_molecule_workload_fdm():
+    """Full-size Poisson solve: FDM-preconditioned CG agrees with Jacobi CG."""
+    cfg = synth.config2()
+    m = Mesh.from_config(cfg)
+    psi = synth.smooth_orbitals(tuple(m.Ni), cfg.n_orb, seed=1)
+    a, b = _ctx(cfg), _ctx(cfg)
+    a.set_cg(1e-12, 5000, 0)
+    b.set_cg(1e-12, 5000, 1)
+    rho = a.density(_cuda(psi))
+    va, ia = a.hartree(rho)
+    vb, ib = b.hartree(rho)
+    assert ia <= 3 < ib
+    assert _rel(va.cpu().numpy(), vb.cpu().numpy()) < 1e-9
 
 
 @pytest.mark.parametrize("kind", ["soft", "bare", "harmonic"])
