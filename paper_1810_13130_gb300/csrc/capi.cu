@@ -122,6 +122,21 @@ tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int
   return TDKS_OK;
 }
 
+// Folded storage of a centrosymmetric n x n matrix (layout in tdks_internal.h).
+void fold_centrosymmetric(const double* M, int n, double* out) {
+  const int h = n / 2;
+  for (int q = 0; q < h; ++q)
+    for (int i = 0; i < h; ++i) {
+      out[q * h + i] = 0.5 * (M[q * n + i] + M[q * n + (n - 1 - i)]);
+      out[h * h + q * h + i] = 0.5 * (M[q * n + i] - M[q * n + (n - 1 - i)]);
+    }
+  double* mc = out + 2 * h * h;
+  double* mr = mc + h;
+  for (int q = 0; q < h; ++q) mc[q] = (n & 1) ? M[q * n + h] : 0.0;
+  for (int i = 0; i < h; ++i) mr[i] = (n & 1) ? M[h * n + i] : 0.0;
+  mr[h] = (n & 1) ? M[h * n + h] : 0.0;
+}
+
 tdks_status check_orb(tdks_ctx* c, int n_orb) {
   if (n_orb < 1 || n_orb > c->n_orb)
     return tdks_fail(c, TDKS_ERR_ARG, "n_orb must be in [1, system n_orb]");
@@ -242,6 +257,15 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
   std::memcpy(&tab[tab_off_K1(P1)], t.K1.data(), P1 * P1 * sizeof(double));
   std::memcpy(&tab[tab_off_Mg(P1)], t.Mg.data(), P1 * P1 * sizeof(double));
   std::memcpy(&tab[tab_off_eta(P1)], t.eta.data(), P1 * sizeof(double));
+  {
+    // folded (even-odd) forms of B (q <- i), B^T (i <- q) and Kq
+    std::vector<double> Bt(P1 * P1);
+    for (int q = 0; q < P1; ++q)
+      for (int i = 0; i < P1; ++i) Bt[i * P1 + q] = t.B[q * P1 + i];
+    fold_centrosymmetric(t.B.data(), P1, &tab[tab_off_csB(P1)]);
+    fold_centrosymmetric(Bt.data(), P1, &tab[tab_off_csBT(P1)]);
+    fold_centrosymmetric(t.Kq.data(), P1, &tab[tab_off_csK(P1)]);
+  }
   std::vector<float> tabf(tab.begin(), tab.end());
   if ((st = upload(c, &c->d_tab, tab)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_tabf, tabf)) != TDKS_OK) return fail(st);

@@ -39,53 +39,69 @@ struct Cfg {
 
 // ---------------------------------------------------------------------------
 // Hbar psibar, complex, contraction type T (double or float)
+//
+// Each thread of an element's P1 x P1 plane owns one full 1-D line in every
+// stage (a z-column, a y-line or an x-line), applies the folded 1-D operator in
+// registers and writes the line back to shared memory:
+//   forward  z (gathered column) -> y -> x            : u~ = B^(x)3 u
+//   x-line:  r = J W V u~ + cx W W (Kq u~)_x           (written to R)
+//   y-line:  R += cy W W (Kq u~)_y;  z-line: r = R + cz W W (Kq u~)_z
+//   backward z -> y -> x (B^T), scatter-add of the x-line with the Loewdin scale.
 // ---------------------------------------------------------------------------
 template <int P1, typename T>
 __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
                                               int color, int orb_per_cta, int part_off) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   typedef Cx<T> V;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[8];
   T* sB = reinterpret_cast<T*>(smem);
-  T* sK = sB + P2;
-  T* sw = sK + P2;
-  const size_t off = ((2 * P2 + P1) * sizeof(T) + 15) & ~size_t(15);
+  T* sBT = sB + CS;
+  T* sK = sBT + CS;
+  T* sw = sK + CS;
+  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
   V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
   V* S2 = S1 + P3;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  for (int i = tid; i < 2 * P2 + P1; i += nthr) sB[i] = tab[i];
-  const int ta = threadIdx.x % P1, tb = threadIdx.x / P1;
+  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
   const bool valid = color_elem(g, color, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
   __syncthreads();
 
-  T ckx = T(0), cky = T(0), ckz = T(0);
-  T vcol[P1];
+  T fx = T(0), fy = T(0), fz = T(0);
+  T vx[P1];
 #pragma unroll
-  for (int q = 0; q < P1; ++q) vcol[q] = T(0);
+  for (int q = 0; q < P1; ++q) vx[q] = T(0);
   if (valid) {
     const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
     const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
     const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
     const double J = 0.125 * hx * hy * hz;
-    ckx = T(hy * hz / (4.0 * hx));
-    cky = T(hx * hz / (4.0 * hy));
-    ckz = T(hx * hy / (4.0 * hz));
+    const double wl = (double)sw[u] * (double)sw[v];
+    fx = T(hy * hz / (4.0 * hx) * wl);
+    fy = T(hx * hz / (4.0 * hy) * wl);
+    fz = T(hx * hy / (4.0 * hz) * wl);
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
-    const double* vp = vks + e * P3 + tb * P1 + ta;
-    const double wab = J * (double)sw[ta] * (double)sw[tb];
+    const double* vp = vks + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
 #pragma unroll
-    for (int q = 0; q < P1; ++q) vcol[q] = T(vp[q * P2] * wab * (double)sw[q]);
+    for (int q = 0; q < P1; ++q) vx[q] = T(vp[q] * J * wl * (double)sw[q]);
   }
-  const int I = ex * g.p + ta, Jn = ey * g.p + tb;
-  const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
-  const double sxy = inIJ ? g.s[0][I] * g.s[1][Jn] : 0.0;
-  const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
   const long long plane = (long long)g.nix * g.niy;
-  const T wa = sw[ta], wb = sw[tb];
+  // gather: z-column (a = u, b = v)
+  const int Ig = ex * g.p + u, Jg = ey * g.p + v;
+  const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
+  const double sG = inG ? g.s[0][Ig] * g.s[1][Jg] : 0.0;
+  const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
+  // scatter: x-line (b = u, c = v)
+  const int Js = ey * g.p + u, Ks = ez * g.p + v;
+  const bool inS = valid && Js >= 1 && Js <= g.niy && Ks >= 1 && Ks <= g.niz;
+  const double sS = inS ? g.s[1][Js] * g.s[2][Ks] : 0.0;
+  const long long baseS = inS ? (long long)g.nix * ((Js - 1) + (long long)g.niy * (Ks - 1)) : 0;
 
   for (int oo = 0; oo < orb_per_cta; ++oo) {
     const int o = blockIdx.y * orb_per_cta + oo;
@@ -96,58 +112,81 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
       sc = a.kry[o].s[a.kj];
     }
     const double2* in = a.in_base + (long long)o * a.in_stride;
-    V u[P1];
+    V col[P1], t[P1];
 #pragma unroll
     for (int c = 0; c < P1; ++c) {
       const int K = ez * g.p + c;
-      vzero(u[c]);
-      if (inIJ && K >= 1 && K <= g.niz) {
-        const double f = sxy * g.s[2][K] * sc;
-        const double2 v = in[base + plane * (K - 1)];
-        u[c].re = T(v.x * f);
-        u[c].im = T(v.y * f);
+      vzero(col[c]);
+      if (inG && K >= 1 && K <= g.niz) {
+        const double f = sG * g.s[2][K] * sc;
+        const double2 w2 = in[baseG + plane * (K - 1)];
+        col[c].re = T(w2.x * f);
+        col[c].im = T(w2.y * f);
       }
     }
-    V uq[P1];
-    forward3<P1, V, T>(u, uq, S1, S2, sB, ta, tb);
-#pragma unroll
-    for (int q = 0; q < P1; ++q) S1[q * P2 + tb * P1 + ta] = uq[q];
+    // forward z, y, x
+    cs_apply<P1>(sB, col, t);
+    store_line(t, S1 + v * P1 + u, P2);
     __syncthreads();
-    V r[P1];
+    load_line(col, S1 + v * P2 + u, P1);
+    cs_apply<P1>(sB, col, t);
+    store_line(t, S2 + v * P2 + u, P1);
+    __syncthreads();
+    V uq[P1];
+    load_line(col, S2 + v * P2 + u * P1, 1);
+    cs_apply<P1>(sB, col, uq);
+    store_line(uq, S1 + v * P2 + u * P1, 1);          // U (Gauss-point values)
+    cs_apply<P1>(sK, uq, t);
+#pragma unroll
+    for (int q = 0; q < P1; ++q) {
+      V r = vscale(vx[q], uq[q]);
+      madd(r, fx, t[q]);
+      t[q] = r;
+    }
+    store_line(t, S2 + v * P2 + u * P1, 1);           // R
+    __syncthreads();
+    // y-line (qx = u, qz = v): R += cy W W (Kq U)_y
+    load_line(col, S1 + v * P2 + u, P1);
+    cs_apply<P1>(sK, col, t);
+#pragma unroll
+    for (int q = 0; q < P1; ++q) {
+      V r = S2[v * P2 + q * P1 + u];
+      madd(r, fy, t[q]);
+      S2[v * P2 + q * P1 + u] = r;
+    }
+    __syncthreads();
+    // z-line (qx = u, qy = v): r = R + cz W W (Kq U)_z
+    load_line(col, S1 + v * P1 + u, P2);
+    cs_apply<P1>(sK, col, t);
     double apart = 0.0;
 #pragma unroll
-    for (int qz = 0; qz < P1; ++qz) {
-      V kz, kx, ky;
-      vzero(kz);
-      vzero(kx);
-      vzero(ky);
-#pragma unroll
-      for (int q = 0; q < P1; ++q) {
-        madd(kz, sK[qz * P1 + q], uq[q]);
-        madd(kx, sK[ta * P1 + q], S1[qz * P2 + tb * P1 + q]);
-        madd(ky, sK[tb * P1 + q], S1[qz * P2 + q * P1 + ta]);
-      }
-      const T wz = sw[qz];
-      const T fz = ckz * wa * wb, fx = ckx * wb * wz, fy = cky * wa * wz;
-      V rr = vscale(vcol[qz], uq[qz]);
-      madd(rr, fz, kz);
-      madd(rr, fx, kx);
-      madd(rr, fy, ky);
-      r[qz] = rr;
-      apart += (double)uq[qz].re * (double)rr.re + (double)uq[qz].im * (double)rr.im;
+    for (int q = 0; q < P1; ++q) {
+      V r = S2[q * P2 + v * P1 + u];
+      madd(r, fz, t[q]);
+      uq[q] = r;
+      apart += (double)col[q].re * (double)r.re + (double)col[q].im * (double)r.im;
     }
-    V y[P1];
-    backward3<P1, V, T>(r, y, S1, S2, sB, ta, tb);
+    __syncthreads();
+    // backward z, y, x
+    cs_apply<P1>(sBT, uq, t);
+    store_line(t, S1 + v * P1 + u, P2);
+    __syncthreads();
+    load_line(col, S1 + v * P2 + u, P1);
+    cs_apply<P1>(sBT, col, t);
+    store_line(t, S2 + v * P2 + u, P1);
+    __syncthreads();
+    load_line(col, S2 + v * P2 + u * P1, 1);
+    cs_apply<P1>(sBT, col, t);
     double2* out = a.out_base + (long long)o * a.out_stride;
 #pragma unroll
-    for (int c = 0; c < P1; ++c) {
-      const int K = ez * g.p + c;
-      if (inIJ && K >= 1 && K <= g.niz) {
-        const double f = sxy * g.s[2][K];
-        const long long idx = base + plane * (K - 1);
+    for (int aa = 0; aa < P1; ++aa) {
+      const int I = ex * g.p + aa;
+      if (inS && I >= 1 && I <= g.nix) {
+        const double f = sS * g.s[0][I];
+        const long long idx = baseS + (I - 1);
         double2 old = out[idx];
-        old.x = fma(f, (double)y[c].re, old.x);
-        old.y = fma(f, (double)y[c].im, old.y);
+        old.x = fma(f, (double)t[aa].re, old.x);
+        old.y = fma(f, (double)t[aa].im, old.y);
         out[idx] = old;
       }
     }
@@ -267,50 +306,77 @@ __global__ void __launch_bounds__(256) k_stiff(Geom g, const double* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Load vector out += (B^T)^(x)3 (J W f_q) (real), Eq. 19 right-hand side
+// Load vector out += (B^T)^(x)3 (J W f_q) (real), Eq. 19 right-hand side:
+// x-lines of the Gauss-point field, then y, then z, scatter of the z-column.
 // ---------------------------------------------------------------------------
 template <int P1>
 __global__ void __launch_bounds__(256) k_load(Geom g, const double* __restrict__ tab,
                                               const double* __restrict__ fq,
                                               double* __restrict__ out, double scale, int color) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  double* sB = reinterpret_cast<double*>(smem);
-  double* sw = sB + P2;
+  double* sBT = reinterpret_cast<double*>(smem);
+  double* sw = sBT + CS;
   double* S1 = sw + P1 + (size_t)threadIdx.y * 2 * P3;
   double* S2 = S1 + P3;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  for (int i = tid; i < P2; i += nthr) sB[i] = tab[i];
+  for (int i = tid; i < CS; i += nthr) sBT[i] = tab[tab_off_csBT(P1) + i];
   for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
-  const int ta = threadIdx.x % P1, tb = threadIdx.x / P1;
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
   const bool valid = color_elem(g, color, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
   __syncthreads();
-  double r[P1];
+  double col[P1], t[P1];
 #pragma unroll
-  for (int q = 0; q < P1; ++q) r[q] = 0.0;
+  for (int q = 0; q < P1; ++q) col[q] = 0.0;
   if (valid) {
     const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
     const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
     const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
-    const double J = 0.125 * hx * hy * hz * scale;
+    const double Jw = 0.125 * hx * hy * hz * scale * sw[u] * sw[v];
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
-    const double* fp = fq + e * P3 + tb * P1 + ta;
+    const double* fp = fq + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
 #pragma unroll
-    for (int q = 0; q < P1; ++q) r[q] = fp[q * P2] * J * sw[ta] * sw[tb] * sw[q];
+    for (int q = 0; q < P1; ++q) col[q] = fp[q] * Jw * sw[q];
   }
-  double y[P1];
-  backward3<P1, double, double>(r, y, S1, S2, sB, ta, tb);
-  const int I = ex * g.p + ta, Jn = ey * g.p + tb;
+  cs_apply<P1>(sBT, col, t);
+  store_line(t, S1 + v * P2 + u * P1, 1);                 // [qz][qy][a]
+  __syncthreads();
+  load_line(col, S1 + v * P2 + u, P1);                    // y-line (a = u, qz = v)
+  cs_apply<P1>(sBT, col, t);
+  store_line(t, S2 + v * P2 + u, P1);                     // [qz][b][a]
+  __syncthreads();
+  load_line(col, S2 + v * P1 + u, P2);                    // z-line (a = u, b = v)
+  cs_apply<P1>(sBT, col, t);
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
   const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
   const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
   const long long plane = (long long)g.nix * g.niy;
 #pragma unroll
   for (int c = 0; c < P1; ++c) {
     const int K = ez * g.p + c;
-    if (inIJ && K >= 1 && K <= g.niz) out[base + plane * (K - 1)] += y[c];
+    if (inIJ && K >= 1 && K <= g.niz) out[base + plane * (K - 1)] += t[c];
   }
+}
+
+// Forward pass of one element: gathered z-column -> Gauss values on the thread's
+// x-line (qy = u, qz = v).  S1, S2 must be free on entry.
+template <int P1, typename V, typename T>
+__device__ __forceinline__ void forward_lines(V (&col)[P1], V (&uq)[P1], V* S1, V* S2,
+                                              const T* sB, int u, int v) {
+  constexpr int P2 = P1 * P1;
+  V t[P1];
+  cs_apply<P1>(sB, col, t);
+  store_line(t, S1 + v * P1 + u, P2);
+  __syncthreads();
+  load_line(col, S1 + v * P2 + u, P1);
+  cs_apply<P1>(sB, col, t);
+  store_line(t, S2 + v * P2 + u, P1);
+  __syncthreads();
+  load_line(col, S2 + v * P2 + u * P1, 1);
+  cs_apply<P1>(sB, col, uq);
 }
 
 // ---------------------------------------------------------------------------
@@ -321,33 +387,32 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const double* __restrict
                                                 const double* __restrict__ nodal,
                                                 double* __restrict__ fq) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   double* sB = reinterpret_cast<double*>(smem);
-  double* S1 = sB + P2 + (size_t)threadIdx.y * 2 * P3;
+  double* S1 = sB + CS + (size_t)threadIdx.y * 2 * P3;
   double* S2 = S1 + P3;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  for (int i = tid; i < P2; i += nthr) sB[i] = tab[i];
-  const int ta = threadIdx.x % P1, tb = threadIdx.x / P1;
+  for (int i = tid; i < CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
   const bool valid = plain_elem(g, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
   __syncthreads();
-  const int I = ex * g.p + ta, Jn = ey * g.p + tb;
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
   const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
   const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
   const long long plane = (long long)g.nix * g.niy;
-  double u[P1];
+  double col[P1], uq[P1];
 #pragma unroll
   for (int c = 0; c < P1; ++c) {
     const int K = ez * g.p + c;
-    u[c] = (inIJ && K >= 1 && K <= g.niz) ? nodal[base + plane * (K - 1)] : 0.0;
+    col[c] = (inIJ && K >= 1 && K <= g.niz) ? nodal[base + plane * (K - 1)] : 0.0;
   }
-  double uq[P1];
-  forward3<P1, double, double>(u, uq, S1, S2, sB, ta, tb);
+  forward_lines<P1, double, double>(col, uq, S1, S2, sB, u, v);
   if (valid) {
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
-#pragma unroll
-    for (int q = 0; q < P1; ++q) fq[e * P3 + q * P2 + tb * P1 + ta] = uq[q];
+    store_line(uq, fq + e * P3 + v * P2 + u * P1, 1);
   }
 }
 
@@ -360,19 +425,21 @@ __global__ void __launch_bounds__(256) k_density(Geom g, const double* __restric
                                                  int n_orb, const double* __restrict__ occ,
                                                  double* __restrict__ rho) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   typedef Cx<double> V;
   extern __shared__ __align__(16) unsigned char smem[];
   double* sB = reinterpret_cast<double*>(smem);
-  V* S1 = reinterpret_cast<V*>(sB + P2) + (size_t)threadIdx.y * 2 * P3;
+  const size_t off = (CS * sizeof(double) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
   V* S2 = S1 + P3;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  for (int i = tid; i < P2; i += nthr) sB[i] = tab[i];
-  const int ta = threadIdx.x % P1, tb = threadIdx.x / P1;
+  for (int i = tid; i < CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
   const bool valid = plain_elem(g, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
   __syncthreads();
-  const int I = ex * g.p + ta, Jn = ey * g.p + tb;
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
   const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
   const double sxy = inIJ ? g.s[0][I] * g.s[1][Jn] : 0.0;
   const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
@@ -382,20 +449,19 @@ __global__ void __launch_bounds__(256) k_density(Geom g, const double* __restric
   for (int q = 0; q < P1; ++q) acc[q] = 0.0;
   for (int o = 0; o < n_orb; ++o) {
     const double2* in = psi + (long long)o * stride;
-    V u[P1];
+    V col[P1], uq[P1];
 #pragma unroll
     for (int c = 0; c < P1; ++c) {
       const int K = ez * g.p + c;
-      vzero(u[c]);
+      vzero(col[c]);
       if (inIJ && K >= 1 && K <= g.niz) {
         const double f = sxy * g.s[2][K];
-        const double2 v = in[base + plane * (K - 1)];
-        u[c].re = v.x * f;
-        u[c].im = v.y * f;
+        const double2 w2 = in[base + plane * (K - 1)];
+        col[c].re = w2.x * f;
+        col[c].im = w2.y * f;
       }
     }
-    V uq[P1];
-    forward3<P1, V, double>(u, uq, S1, S2, sB, ta, tb);
+    forward_lines<P1, V, double>(col, uq, S1, S2, sB, u, v);
     const double f = occ[o];
 #pragma unroll
     for (int q = 0; q < P1; ++q) acc[q] += f * (uq[q].re * uq[q].re + uq[q].im * uq[q].im);
@@ -403,8 +469,7 @@ __global__ void __launch_bounds__(256) k_density(Geom g, const double* __restric
   }
   if (valid) {
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
-#pragma unroll
-    for (int q = 0; q < P1; ++q) rho[e * P3 + q * P2 + tb * P1 + ta] = acc[q];
+    store_line(acc, rho + e * P3 + v * P2 + u * P1, 1);
   }
 }
 
@@ -429,7 +494,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <int P1, typename T>
 tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
-  const size_t smem = (((2 * P2 + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
   TDKS_CU(c, set_smem(k_hbar<P1, T>, smem));
   const int bpc = blocks_per_color_t<P1>(c);
   // orbitals per CTA: enough CTAs to fill the GPU, V and geometry reused across orbitals
@@ -466,7 +532,8 @@ tdks_status stiff_t(tdks_ctx* c, const double* in, double* out, double* part, co
 template <int P1>
 tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
-  const size_t smem = (P2 + P1 + (size_t)E * 2 * P3) * sizeof(double);
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = (CS + P1 + (size_t)E * 2 * P3) * sizeof(double);
   TDKS_CU(c, set_smem(k_load<P1>, smem));
   dim3 block(P2, E), grid(blocks_per_color_t<P1>(c));
   const Geom g = tdks_geom(c);
@@ -480,7 +547,8 @@ tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale) {
 template <int P1>
 tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
-  const size_t smem = (P2 + (size_t)E * 2 * P3) * sizeof(double);
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = (CS + (size_t)E * 2 * P3) * sizeof(double);
   TDKS_CU(c, set_smem(k_interp<P1>, smem));
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
   k_interp<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, nodal, fq);
@@ -492,7 +560,8 @@ tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq) {
 template <int P1>
 tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
-  const size_t smem = P2 * sizeof(double) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = ((CS * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
   TDKS_CU(c, set_smem(k_density<P1>, smem));
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
   k_density<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, psi, c->n_int, n_orb,

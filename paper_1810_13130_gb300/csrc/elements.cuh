@@ -2,11 +2,11 @@
 //
 // An element holds (p+1)^3 nodal values u[c][b][a] (a along x fastest).  Each
 // CTA runs E elements side by side, one 2-D thread plane (P1 x P1 threads) per
-// element: thread (ta, tb) owns the z-column of values at (a = ta, b = tb) in
-// registers.  A 1-D contraction along z is done in registers; along y and x the
-// plane goes through shared memory.  With nq = p+1 Gauss points the "nodal ->
-// Gauss point" map B is square, so forward (B (x) B (x) B) and backward
-// (B^T (x) B^T (x) B^T) passes are three contractions each.
+// element.  In every stage each thread owns one complete 1-D line of the element
+// cube (along z, y or x), applies a 1-D operator to it in registers and writes it
+// back to shared memory.  With nq = p+1 Gauss points the "nodal -> Gauss point"
+// map B is square, so forward (B (x) B (x) B) and backward (B^T (x) B^T (x) B^T)
+// passes are three contractions each.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,9 +33,71 @@ __device__ __forceinline__ void madd(Cx<T>& acc, T c, const Cx<T>& v) {
   acc.im = fma(c, v.im, acc.im);
 }
 template <typename T>
+__device__ __forceinline__ T vadd(const T& a, const T& b) { return a + b; }
+template <typename T>
+__device__ __forceinline__ Cx<T> vadd(const Cx<T>& a, const Cx<T>& b) { return Cx<T>{a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ T vsub(const T& a, const T& b) { return a - b; }
+template <typename T>
+__device__ __forceinline__ Cx<T> vsub(const Cx<T>& a, const Cx<T>& b) { return Cx<T>{a.re - b.re, a.im - b.im}; }
+template <typename T>
 __device__ __forceinline__ T vscale(T c, const T& v) { return c * v; }
 template <typename T>
 __device__ __forceinline__ Cx<T> vscale(T c, const Cx<T>& v) { return Cx<T>{c * v.re, c * v.im}; }
+
+// out = M in for a centrosymmetric N x N matrix M stored folded (layout in
+// tdks_internal.h): pairs (i, N-1-i) of the input are combined into even and odd
+// parts e_i = in_i + in_{N-1-i}, o_i = in_i - in_{N-1-i}, so that
+//   out_q = a_q + b_q,  out_{N-1-q} = a_q - b_q,  a_q = sum_i Me[q][i] e_i (+ M[q][h] in_h),
+//   b_q = sum_i Mo[q][i] o_i,  out_h = sum_i M[h][i] e_i + M[h][h] in_h  (odd N):
+// about N^2/2 multiply-adds instead of N^2.
+template <int N, typename V, typename T>
+__device__ __forceinline__ void cs_apply(const T* __restrict__ t, const V (&in)[N], V (&out)[N]) {
+  constexpr int h = N / 2;
+  constexpr int hh = h > 0 ? h : 1;
+  const T* Me = t;
+  const T* Mo = t + h * h;
+  const T* Mc = t + 2 * h * h;
+  const T* Mr = Mc + h;
+  V e[hh], o[hh];
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    e[i] = vadd(in[i], in[N - 1 - i]);
+    o[i] = vsub(in[i], in[N - 1 - i]);
+  }
+#pragma unroll
+  for (int q = 0; q < h; ++q) {
+    V a, b;
+    vzero(a);
+    vzero(b);
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      madd(a, Me[q * h + i], e[i]);
+      madd(b, Mo[q * h + i], o[i]);
+    }
+    if (N & 1) madd(a, Mc[q], in[h]);
+    out[q] = vadd(a, b);
+    out[N - 1 - q] = vsub(a, b);
+  }
+  if (N & 1) {
+    V c = vscale(Mr[h], in[h]);
+#pragma unroll
+    for (int i = 0; i < h; ++i) madd(c, Mr[i], e[i]);
+    out[h] = c;
+  }
+}
+
+template <int N, typename V>
+__device__ __forceinline__ void load_line(V (&r)[N], const V* src, int stride) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) r[i] = src[i * stride];
+}
+
+template <int N, typename V>
+__device__ __forceinline__ void store_line(const V (&r)[N], V* dst, int stride) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[i * stride] = r[i];
+}
 
 // Element of a parity colour: colour bits (cx, cy, cz) select ex = cx + 2 gx etc.
 // Elements of one colour share no node, so a launch can read-modify-write its
@@ -65,82 +127,6 @@ __device__ __forceinline__ bool plain_elem(const Geom& g, long long gidx, int& e
   ey = (int)(r % g.ny);
   ez = (int)(r / g.ny);
   return true;
-}
-
-// Forward pass: column u[c] (registers) -> values at the Gauss points,
-// returned as the z-column uq[qz] of thread (qx = ta, qy = tb).
-template <int P1, typename V, typename T>
-__device__ __forceinline__ void forward3(const V (&u)[P1], V (&uq)[P1], V* S1, V* S2,
-                                         const T* sB, int ta, int tb) {
-  constexpr int P2 = P1 * P1;
-  V t[P1];
-#pragma unroll
-  for (int q = 0; q < P1; ++q) vzero(t[q]);
-#pragma unroll
-  for (int c = 0; c < P1; ++c)
-#pragma unroll
-    for (int q = 0; q < P1; ++q) madd(t[q], sB[q * P1 + c], u[c]);
-#pragma unroll
-  for (int q = 0; q < P1; ++q) S1[q * P2 + tb * P1 + ta] = t[q];
-  __syncthreads();
-  // y: thread (a = ta, qy = tb)
-#pragma unroll
-  for (int qz = 0; qz < P1; ++qz) {
-    V acc;
-    vzero(acc);
-#pragma unroll
-    for (int b = 0; b < P1; ++b) madd(acc, sB[tb * P1 + b], S1[qz * P2 + b * P1 + ta]);
-    S2[qz * P2 + tb * P1 + ta] = acc;
-  }
-  __syncthreads();
-  // x: thread (qx = ta, qy = tb)
-#pragma unroll
-  for (int qz = 0; qz < P1; ++qz) {
-    V acc;
-    vzero(acc);
-#pragma unroll
-    for (int a = 0; a < P1; ++a) madd(acc, sB[ta * P1 + a], S2[qz * P2 + tb * P1 + a]);
-    uq[qz] = acc;
-  }
-}
-
-// Backward pass: z-column r[qz] of thread (qx = ta, qy = tb) at the Gauss points
-// -> nodal column y[c] of thread (a = ta, b = tb), y = (B^T (x) B^T (x) B^T) r.
-// Starts with a barrier so that S1/S2 may still be in use on entry.
-template <int P1, typename V, typename T>
-__device__ __forceinline__ void backward3(const V (&r)[P1], V (&y)[P1], V* S1, V* S2,
-                                          const T* sB, int ta, int tb) {
-  constexpr int P2 = P1 * P1;
-  V t[P1];
-#pragma unroll
-  for (int c = 0; c < P1; ++c) vzero(t[c]);
-#pragma unroll
-  for (int q = 0; q < P1; ++q)
-#pragma unroll
-    for (int c = 0; c < P1; ++c) madd(t[c], sB[q * P1 + c], r[q]);
-  __syncthreads();
-#pragma unroll
-  for (int c = 0; c < P1; ++c) S1[c * P2 + tb * P1 + ta] = t[c];
-  __syncthreads();
-  // y: thread (qx = ta, b = tb)
-#pragma unroll
-  for (int c = 0; c < P1; ++c) {
-    V acc;
-    vzero(acc);
-#pragma unroll
-    for (int q = 0; q < P1; ++q) madd(acc, sB[q * P1 + tb], S1[c * P2 + q * P1 + ta]);
-    S2[c * P2 + tb * P1 + ta] = acc;
-  }
-  __syncthreads();
-  // x: thread (a = ta, b = tb)
-#pragma unroll
-  for (int c = 0; c < P1; ++c) {
-    V acc;
-    vzero(acc);
-#pragma unroll
-    for (int q = 0; q < P1; ++q) madd(acc, sB[q * P1 + ta], S2[c * P2 + tb * P1 + q]);
-    y[c] = acc;
-  }
 }
 
 // Deterministic block sum (fixed shuffle tree); result valid in thread 0.

@@ -149,13 +149,23 @@ void tdks_fdm_axis(const Tables1D& t, int p, const double* br, int n_el, std::ve
 
 // Device table layout (both double and float copies), offsets in elements.
 //   B [P1*P1] | Kq [P1*P1] | w [P1] | K1 [P1*P1] | Mg [P1*P1] | eta [P1]
+//   | csB | csBT | csKq      (even-odd folded forms, see cs_apply in elements.cuh)
+// A centrosymmetric n x n matrix M (M[n-1-i][n-1-j] = M[i][j]) is stored folded as
+// Me[h][h] = (M[q][i] + M[q][n-1-i])/2, Mo[h][h] = (M[q][i] - M[q][n-1-i])/2 for
+// q, i < h = n/2, then (odd n) the middle column M[q][h], the middle row M[h][i]
+// and M[h][h].  B, B^T and Kq are centrosymmetric because the GLL nodes and the
+// Gauss points are symmetric about 0.
+TDKS_HD inline int cs_size(int P1) { return 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1; }
 TDKS_HD inline int tab_off_B(int) { return 0; }
 TDKS_HD inline int tab_off_Kq(int P1) { return P1 * P1; }
 TDKS_HD inline int tab_off_w(int P1) { return 2 * P1 * P1; }
 TDKS_HD inline int tab_off_K1(int P1) { return 2 * P1 * P1 + P1; }
 TDKS_HD inline int tab_off_Mg(int P1) { return 3 * P1 * P1 + P1; }
 TDKS_HD inline int tab_off_eta(int P1) { return 4 * P1 * P1 + P1; }
-TDKS_HD inline int tab_size(int P1) { return 4 * P1 * P1 + 2 * P1; }
+TDKS_HD inline int tab_off_csB(int P1) { return 4 * P1 * P1 + 2 * P1; }
+TDKS_HD inline int tab_off_csBT(int P1) { return tab_off_csB(P1) + cs_size(P1); }
+TDKS_HD inline int tab_off_csK(int P1) { return tab_off_csBT(P1) + cs_size(P1); }
+TDKS_HD inline int tab_size(int P1) { return tab_off_csK(P1) + cs_size(P1); }
 
 // ---------------------------------------------------------------- launchers
 // element kernels (elements.cu)
