@@ -87,6 +87,7 @@ void free_ctx(tdks_ctx* c) {
   cudaFree(c->d_V);
   cudaFree(c->d_kry);
   cudaFree(c->d_psi_half);
+  cudaFree(c->d_evec);
   cudaFree(c->d_psi_e2e);
   cudaFree(c->d_part);
   cudaFree(c->d_z);
@@ -352,8 +353,8 @@ tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb,
   if (!c || !psi || !out) return TDKS_ERR_ARG;
   if (n_orb < 1) return tdks_fail(c, TDKS_ERR_ARG, "n_orb >= 1");
   if (prec != TDKS_FP64 && prec != TDKS_FP32) return tdks_fail(c, TDKS_ERR_ARG, "precision");
-  TDKS_CU(c, cudaMemsetAsync(out, 0, (size_t)n_orb * c->n_int * sizeof(double2), c->stream));
-  ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0};
+  ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0,
+              0, nullptr, 0, nullptr, 0};
   c->n_apply_units += (int64_t)n_orb * c->n_elem;
   return launch_hbar_apply(c, a, prec);
 }

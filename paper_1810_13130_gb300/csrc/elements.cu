@@ -51,7 +51,7 @@ struct Cfg {
 template <int P1, typename T>
 __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
-                                              int color, int orb_per_cta, int part_off) {
+                                              int orb_per_cta, Cx<T>* __restrict__ ev) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   typedef Cx<T> V;
@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
   for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
-  const bool valid = color_elem(g, color, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const bool valid = plain_elem(g, eidx, ex, ey, ez);
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
   __syncthreads();
 
   T fx = T(0), fy = T(0), fz = T(0);
@@ -97,11 +99,6 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
   const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
   const double sG = inG ? g.s[0][Ig] * g.s[1][Jg] : 0.0;
   const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
-  // scatter: x-line (b = u, c = v)
-  const int Js = ey * g.p + u, Ks = ez * g.p + v;
-  const bool inS = valid && Js >= 1 && Js <= g.niy && Ks >= 1 && Ks <= g.niz;
-  const double sS = inS ? g.s[1][Js] * g.s[2][Ks] : 0.0;
-  const long long baseS = inS ? (long long)g.nix * ((Js - 1) + (long long)g.niy * (Ks - 1)) : 0;
 
   for (int oo = 0; oo < orb_per_cta; ++oo) {
     const int o = blockIdx.y * orb_per_cta + oo;
@@ -177,24 +174,114 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
     __syncthreads();
     load_line(col, S2 + v * P2 + u * P1, 1);
     cs_apply<P1>(sBT, col, t);
-    double2* out = a.out_base + (long long)o * a.out_stride;
-#pragma unroll
-    for (int aa = 0; aa < P1; ++aa) {
-      const int I = ex * g.p + aa;
-      if (inS && I >= 1 && I <= g.nix) {
-        const double f = sS * g.s[0][I];
-        const long long idx = baseS + (I - 1);
-        double2 old = out[idx];
-        old.x = fma(f, (double)t[aa].re, old.x);
-        old.y = fma(f, (double)t[aa].im, old.y);
-        out[idx] = old;
-      }
-    }
+    if (valid) store_line(t, ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1, 1);
     if (a.part) {
       const double s = block_sum(apart, red);
-      if (tid == 0) a.part[(long long)o * a.part_stride + part_off + blockIdx.x] = s;
+      if (tid == 0) a.part[(long long)o * a.part_stride + blockIdx.x] = s;
     }
     __syncthreads();
+  }
+}
+
+// alpha_j = sum of the element partials (fixed order), for the active orbitals
+__global__ void k_alpha(KryOrb* kry, const double* part, int64_t pstride, int nparts, int j) {
+  __shared__ double red[8];
+  const int o = blockIdx.x;
+  if (kry[o].status != KRY_ACTIVE) return;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) v += part[(long long)o * pstride + k];
+  const double s = block_sum(v, red);
+  if (threadIdx.x == 0) kry[o].alpha[j] = s;
+}
+
+// Elements whose closure holds node I along one axis: 1 (inside an element) or 2
+// (on a shared face), with the node's local index in each.
+__device__ __forceinline__ int node_elems(int I, int p, int n, int* e, int* loc) {
+  const int eh = I / p, l = I - eh * p;
+  if (l != 0) {
+    e[0] = eh;
+    loc[0] = l;
+    return 1;
+  }
+  int k = 0;
+  if (eh - 1 >= 0) {
+    e[k] = eh - 1;
+    loc[k] = p;
+    ++k;
+  }
+  if (eh < n) {
+    e[k] = eh;
+    loc[k] = 0;
+    ++k;
+  }
+  return k;
+}
+
+// Assembly by gathering: every interior node sums its (at most 8) element-local
+// contributions in a fixed order and applies the Loewdin scale.  With `lanczos`
+// the three-term update w = Hbar q_j - alpha_j q_j - beta_{j-1} q_{j-1} is fused
+// and the per-block partials of ||w||^2 are written.
+template <typename T>
+__global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* __restrict__ ev,
+                                                  ApplyArgs a) {
+  __shared__ double red[4];
+  const int o = blockIdx.y;
+  double ca = 0.0, cb = 0.0;
+  if (a.kry) {
+    const KryOrb& K = a.kry[o];
+    if (K.status != KRY_ACTIVE) return;
+    if (a.lanczos) {
+      ca = K.alpha[a.kj] * K.s[a.kj];
+      cb = a.kj > 0 ? K.beta[a.kj - 1] * K.s[a.kj - 1] : 0.0;
+    }
+  }
+  const int P2 = P1 * P1;
+  const long long P3 = (long long)P2 * P1;
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  const Cx<T>* evo = ev + (long long)o * n_elem * P3;
+  const double2* qj = a.in_base + (long long)o * a.in_stride;
+  const double2* qm = a.vm_base ? a.vm_base + (long long)o * a.vm_stride : nullptr;
+  double2* out = a.out_base + (long long)o * a.out_stride;
+  const int rows = g.niy * g.niz;
+  double acc = 0.0;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int J = r % g.niy + 1, K = r / g.niy + 1;
+    int ey[2], by[2], ez[2], bz[2], ex[2], bx[2];
+    const int ny = node_elems(J, g.p, g.ny, ey, by);
+    const int nz = node_elems(K, g.p, g.nz, ez, bz);
+    const double syz = g.s[1][J] * g.s[2][K];
+    const long long rowbase = (long long)g.nix * (r);
+    for (int I = threadIdx.x + 1; I <= g.nix; I += blockDim.x) {
+      const int nx = node_elems(I, g.p, g.nx, ex, bx);
+      double re = 0.0, im = 0.0;
+      for (int kz = 0; kz < nz; ++kz)
+        for (int ky = 0; ky < ny; ++ky)
+          for (int kx = 0; kx < nx; ++kx) {
+            const long long e = ex[kx] + (long long)g.nx * (ey[ky] + (long long)g.ny * ez[kz]);
+            const Cx<T> c = evo[e * P3 + bz[kz] * P2 + by[ky] * P1 + bx[kx]];
+            re += (double)c.re;
+            im += (double)c.im;
+          }
+      const double f = g.s[0][I] * syz;
+      const long long idx = rowbase + (I - 1);
+      double2 w = make_double2(f * re, f * im);
+      if (a.lanczos) {
+        const double2 x = qj[idx];
+        w.x = fma(-ca, x.x, w.x);
+        w.y = fma(-ca, x.y, w.y);
+        if (qm) {
+          const double2 y = qm[idx];
+          w.x = fma(-cb, y.x, w.x);
+          w.y = fma(-cb, y.y, w.y);
+        }
+        acc = fma(w.x, w.x, fma(w.y, w.y, acc));
+      }
+      out[idx] = w;
+    }
+  }
+  if (a.npart) {
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) a.npart[(long long)o * a.npart_stride + blockIdx.x] = s;
   }
 }
 
@@ -491,25 +578,43 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <int P1>
+int elem_blocks_t(const tdks_ctx* c) {
+  return (int)((c->n_elem + Cfg<P1>::E - 1) / Cfg<P1>::E);
+}
+
 template <int P1, typename T>
 tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
   TDKS_CU(c, set_smem(k_hbar<P1, T>, smem));
-  const int bpc = blocks_per_color_t<P1>(c);
-  // orbitals per CTA: enough CTAs to fill the GPU, V and geometry reused across orbitals
+  const size_t need = (size_t)a.n_orb * c->n_elem * P3 * sizeof(Cx<T>);
+  if (need > c->evec_bytes) {
+    cudaFree(c->d_evec);
+    c->d_evec = nullptr;
+    c->evec_bytes = 0;
+    if (cudaMalloc(&c->d_evec, need) != cudaSuccess) {
+      cudaGetLastError();
+      return tdks_fail(c, TDKS_ERR_NOMEM, "element-result buffer");
+    }
+    c->evec_bytes = need;
+  }
+  Cx<T>* ev = static_cast<Cx<T>*>(c->d_evec);
+  const int bpe = elem_blocks_t<P1>(c);
+  // orbitals per CTA: V and geometry are reused across them; keep >= 4 CTAs per SM
   int opc = 1;
-  while (opc < a.n_orb && (long long)bpc * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
+  while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
   const int ochunks = (a.n_orb + opc - 1) / opc;
-  dim3 block(P2, E), grid(bpc, ochunks);
   const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab : (const T*)c->d_tabf;
   const Geom g = tdks_geom(c);
-  for (int color = 0; color < 8; ++color) {
-    k_hbar<P1, T><<<grid, block, smem, c->stream>>>(g, tab, c->d_vks, a, color, opc, color * bpc);
-  }
-  c->n_launch += 8;
-  c->n_apply_launch += 8;
+  k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
+  if (a.lanczos && a.kry && a.part)
+    k_alpha<<<a.n_orb, 256, 0, c->stream>>>(a.kry, a.part, a.part_stride, bpe, a.kj);
+  const int gx = assemble_blocks(c, a.n_orb);
+  k_assemble<T><<<dim3(gx, a.n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  c->n_launch += (a.lanczos && a.kry && a.part) ? 3 : 2;
+  c->n_apply_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
@@ -587,10 +692,34 @@ tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho) {
 }  // namespace
 
 int hbar_blocks_per_color(const tdks_ctx* c) {
+  int b = 0;
+  switch (c->P1) {
+    case 2: b = elem_blocks_t<2>(c); break;
+    case 3: b = elem_blocks_t<3>(c); break;
+    case 4: b = elem_blocks_t<4>(c); break;
+    case 5: b = elem_blocks_t<5>(c); break;
+    case 6: b = elem_blocks_t<6>(c); break;
+    case 7: b = elem_blocks_t<7>(c); break;
+    case 8: b = elem_blocks_t<8>(c); break;
+    case 9: b = elem_blocks_t<9>(c); break;
+    default: break;
+  }
+  const int bs = stiff_blocks_per_color(c);
+  return b > bs ? b : bs;
+}
+
+int stiff_blocks_per_color(const tdks_ctx* c) {
   TDKS_DISPATCH(c->P1, blocks_per_color_t<P1>(c));
   return 0;
 }
-int stiff_blocks_per_color(const tdks_ctx* c) { return hbar_blocks_per_color(c); }
+
+int assemble_blocks(const tdks_ctx* c, int n_orb) {
+  const int rows = c->Ni[1] * c->Ni[2];
+  int gx = 2048 / (n_orb > 0 ? n_orb : 1);
+  if (gx < 64) gx = 64;
+  if (gx > 2048) gx = 2048;
+  return rows < gx ? rows : gx;
+}
 
 tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec) {
   if (prec == TDKS_FP32) {

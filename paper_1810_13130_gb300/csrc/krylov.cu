@@ -7,8 +7,9 @@
 //   y = exp(-i tau T_{j+1}) e_1,  eps = tau beta_j ||psi|| |y_j|,  stop at eps <= tol
 //   psi_out = ||psi|| sum_j y_j q_j
 // Basis vectors are stored unnormalized (V_j) with q_j = s_j V_j, and s_j is
-// folded into the next apply's gather.  alpha_j comes out of the apply kernel
-// as sum_e u_e^H H_e u_e (element partial sums), beta_j from the update kernel.
+// folded into the next apply's gather.  alpha_j comes out of the element kernel
+// as sum_e u_e^H H_e u_e (element partial sums); the three-term update and the
+// partial sums of beta_j^2 are fused into the assembly of Hbar q_j.
 //
 // The small exponential exp(-i tau T) e_1 of the real symmetric tridiagonal T
 // is evaluated on the device by the Chebyshev (Jacobi-Anger) expansion
@@ -104,41 +105,6 @@ __global__ void k_kry_start(KryOrb* kry, const double* part, int64_t pstride, in
       K.s[0] = 1.0 / nrm;
     }
   }
-}
-
-// w = V_{j+1} - alpha_j s_j V_j - beta_{j-1} s_{j-1} V_{j-1} (in place), partial ||w||^2
-__global__ void k_kry_update(int j, long long n, double2* Vn, int64_t sn, const double2* Vj,
-                             int64_t sj, const double2* Vm, int64_t sm, KryOrb* kry,
-                             const double* apart, int64_t apstride, int napart, double* npart,
-                             int64_t npstride) {
-  __shared__ double red[kThreads / 32];
-  const int o = blockIdx.y;
-  KryOrb& K = kry[o];
-  if (K.status != KRY_ACTIVE) return;
-  const double alpha = sum_fixed(apart + (long long)o * apstride, napart, red);
-  if (blockIdx.x == 0 && threadIdx.x == 0) K.alpha[j] = alpha;
-  const double a = alpha * K.s[j];
-  const double b = (j > 0) ? K.beta[j - 1] * K.s[j - 1] : 0.0;
-  double2* w = Vn + (long long)o * sn;
-  const double2* x = Vj + (long long)o * sj;
-  const double2* y = (j > 0) ? Vm + (long long)o * sm : nullptr;
-  double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    double2 v = w[i];
-    const double2 u = x[i];
-    v.x = fma(-a, u.x, v.x);
-    v.y = fma(-a, u.y, v.y);
-    if (y) {
-      const double2 t = y[i];
-      v.x = fma(-b, t.x, v.x);
-      v.y = fma(-b, t.y, v.y);
-    }
-    w[i] = v;
-    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
-  }
-  const double s = block_reduce_sum(acc, red);
-  if (threadIdx.x == 0) npart[(long long)o * npstride + blockIdx.x] = s;
 }
 
 // ---- small exponential on one warp -----------------------------------------
@@ -441,6 +407,7 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
   double* apart = c->d_part;
   double* npart = c->d_part + (int64_t)c->n_orb * ps;
   const int nb = grid_for(n);
+  const int nasm = assemble_blocks(c, n_orb);   // partials of ||w||^2 per orbital
   const int64_t wsorb = (int64_t)kmax * n;   // stride between orbitals in the workspace
   std::vector<KrySummary> h(n_orb);
   k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb, tau);
@@ -463,18 +430,14 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
       const double2* Vm = (j == 1) ? cur : (j >= 2 ? c->d_V + (int64_t)(j - 2) * n : nullptr);
       const int64_t sm = (j == 1) ? n : wsorb;
       double2* Vn = c->d_V + (int64_t)j * n;
-      TDKS_CU(c, cudaMemset2DAsync(Vn, wsorb * sizeof(double2), 0, n * sizeof(double2), n_orb,
-                                   c->stream));
-      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, c->d_kry, j, apart, ps};
+      // Hbar q_j and the three-term update fused: V_{j+1} = Hbar q_j - alpha_j q_j - beta q_{j-1}
+      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, c->d_kry, j, apart, ps, 1, Vm, sm, npart, ps};
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[0], c->stream));
       TDKS_TRY(launch_hbar_apply(c, a, prec));
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
       c->n_apply_units += (int64_t)n_active * c->n_elem;
-      k_kry_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(j, n, Vn, wsorb, Vj, sj, Vm, sm,
-                                                               c->d_kry, apart, ps, 8 * bpc, npart,
-                                                               ps);
-      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, c->d_kry, npart, ps, nb);
-      c->n_launch += 2;
+      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, c->d_kry, npart, ps, nasm);
+      c->n_launch += 1;
       TDKS_CU(c, cudaGetLastError());
       TDKS_TRY(read_summary(c, n_orb, h.data()));
       if (c->timing) {

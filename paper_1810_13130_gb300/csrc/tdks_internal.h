@@ -97,6 +97,8 @@ struct tdks_ctx {
   KryOrb* d_kry = nullptr;
   KryOrb* h_kry = nullptr;     // pinned mirror (status reads)
   double2* d_psi_half = nullptr;
+  void* d_evec = nullptr;      // element-local Hbar results [n_orb][n_elem][P1^3] (complex)
+  size_t evec_bytes = 0;
   double2* d_psi_e2e = nullptr;
   // reductions
   double* d_part = nullptr;    // partial sums
@@ -170,15 +172,21 @@ TDKS_HD inline int tab_size(int P1) { return tab_off_csK(P1) + cs_size(P1); }
 // ---------------------------------------------------------------- launchers
 // element kernels (elements.cu)
 struct ApplyArgs {
-  const double2* in_base;
+  const double2* in_base;     // q_j = s[kj] * V_j (V_j when kry is null)
   int64_t in_stride;
-  double2* out_base;
+  double2* out_base;          // Hbar q_j, or the Lanczos residual when `lanczos`
   int64_t out_stride;
   int n_orb;
-  const KryOrb* kry;          // optional: scale s[kj], skip non-active orbitals
+  KryOrb* kry;                // optional: scale s[kj], skip non-active orbitals
   int kj;
-  double* part;               // optional: per-block partial of Re(u^H Hu) per orbital
+  double* part;               // optional: per-block partials of Re(u^H H u) per orbital
   int64_t part_stride;
+  // fused Lanczos update: out = Hbar q_j - alpha_j s_j V_j - beta_{j-1} s_{j-1} V_{j-1}
+  int lanczos;
+  const double2* vm_base;     // V_{j-1} (null when kj == 0)
+  int64_t vm_stride;
+  double* npart;              // per-block partials of ||out||^2 per orbital
+  int64_t npart_stride;
 };
 tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec);
 tdks_status launch_stiffness(tdks_ctx* c, const double* in, double* out, double* part,
@@ -187,6 +195,7 @@ tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, doub
 tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q);
 tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q);
 int hbar_blocks_per_color(const tdks_ctx* c);
+int assemble_blocks(const tdks_ctx* c, int n_orb);   // partial-sum count of the fused update
 int stiff_blocks_per_color(const tdks_ctx* c);
 
 // fields.cu
