@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-only", action="store_true",
@@ -223,7 +223,7 @@ def ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = tdks.FP64 if args.prec == "fp64" else tdks.FP32
+    prec = {"fp64": tdks.FP64, "fp32": tdks.FP32, "df64": tdks.DF64}[args.prec]
     cfg = synth.config2()
     ctx = tdks.Context.from_config(cfg)
     ctx.set_cg(1e-10)
@@ -342,7 +342,7 @@ def apply_only(args, local_rank: int):
     import synth
     from paper_1810_13130_gb300 import tdks
     torch.cuda.set_device(local_rank)
-    prec = tdks.FP64 if args.prec == "fp64" else tdks.FP32
+    prec = {"fp64": tdks.FP64, "fp32": tdks.FP32, "df64": tdks.DF64}[args.prec]
     cfg = synth.config2()
     ctx = tdks.Context.from_config(cfg)
     psi = torch.from_numpy(synth.random_psi(cfg.n_orb, ctx.n_int, seed=3)).cuda()

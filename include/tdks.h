@@ -58,7 +58,9 @@ typedef enum {
  * recurrence, small exponential, Poisson, density and dipole are always FP64. */
 typedef enum {
   TDKS_FP64 = 0,   /* double contractions                                  */
-  TDKS_FP32 = 1    /* float contractions with float accumulation, FP64 I/O  */
+  TDKS_FP32 = 1,   /* float contractions with float accumulation, FP64 I/O  */
+  TDKS_DF64 = 2    /* double-float (compensated float-pair) contractions:
+                      ~48-bit accurate products and sums on the FP32 pipe   */
 } tdks_prec;
 
 typedef enum {

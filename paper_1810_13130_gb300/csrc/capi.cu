@@ -31,6 +31,7 @@ Geom tdks_geom(const tdks_ctx* c) {
   for (int d = 0; d < 3; ++d) {
     g.brk[d] = c->d_brk[d];
     g.s[d] = c->d_s[d];
+    g.sf[d] = c->d_sf[d];
   }
   g.gauss = c->d_tab + tab_off_eta(c->P1);
   return g;
@@ -62,12 +63,14 @@ void free_ctx(tdks_ctx* c) {
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->d_brk[d]);
     cudaFree(c->d_s[d]);
+    cudaFree(c->d_sf[d]);
     cudaFree(c->d_coord[d]);
     cudaFree(c->d_kd[d]);
     cudaFree(c->d_md[d]);
   }
   cudaFree(c->d_tab);
   cudaFree(c->d_tabf);
+  cudaFree(c->d_tabdf);
   cudaFree(c->d_occ);
   cudaFree(c->d_R);
   cudaFree(c->d_Z);
@@ -245,6 +248,8 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
     if ((st = upload(c, &c->d_brk[d], c->brk[d])) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_coord[d], coord)) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_s[d], sv)) != TDKS_OK) return fail(st);
+    std::vector<float> svf(sv.begin(), sv.end());
+    if ((st = upload(c, &c->d_sf[d], svf)) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_kd[d], kd)) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_md[d], md)) != TDKS_OK) return fail(st);
   }
@@ -268,6 +273,13 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
     fold_centrosymmetric(t.Kq.data(), P1, &tab[tab_off_csK(P1)]);
   }
   std::vector<float> tabf(tab.begin(), tab.end());
+  std::vector<float> tabdf(2 * tab.size());
+  for (size_t k = 0; k < tab.size(); ++k) {
+    const float hi = (float)tab[k];
+    tabdf[2 * k] = hi;
+    tabdf[2 * k + 1] = (float)(tab[k] - (double)hi);
+  }
+  if ((st = upload(c, &c->d_tabdf, tabdf)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_tab, tab)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_tabf, tabf)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_occ, c->occ)) != TDKS_OK) return fail(st);
@@ -352,7 +364,8 @@ tdks_status tdks_nuclear_potential(tdks_ctx* c, double* v) {
 tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb, int prec) {
   if (!c || !psi || !out) return TDKS_ERR_ARG;
   if (n_orb < 1) return tdks_fail(c, TDKS_ERR_ARG, "n_orb >= 1");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32) return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+    return tdks_fail(c, TDKS_ERR_ARG, "precision");
   ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0,
               0, nullptr, 0, nullptr, 0};
   c->n_apply_units += (int64_t)n_orb * c->n_elem;
@@ -385,7 +398,8 @@ tdks_status tdks_expm(tdks_ctx* c, const double* in, double* out, int n_orb, dou
   if (!c || !in || !out) return TDKS_ERR_ARG;
   TDKS_TRY(check_orb(c, n_orb));
   if (!(tol > 0) || !std::isfinite(tau)) return tdks_fail(c, TDKS_ERR_ARG, "tol > 0, finite tau");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32) return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+    return tdks_fail(c, TDKS_ERR_ARG, "precision");
   if (in != out)
     TDKS_CU(c, cudaMemcpyAsync(out, in, (size_t)n_orb * c->n_int * sizeof(double2),
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -419,7 +433,8 @@ tdks_status tdks_magnus_step(tdks_ctx* c, double* psi_d, int n_orb, double dt, c
   TDKS_TRY(check_orb(c, n_orb));
   if (!c->propagation_ready) return tdks_fail(c, TDKS_ERR_ARG, "call tdks_init_propagation first");
   if (!(dt > 0) || !(tol > 0)) return tdks_fail(c, TDKS_ERR_ARG, "dt > 0 and tol > 0");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32) return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+    return tdks_fail(c, TDKS_ERR_ARG, "precision");
   double2* psi = (double2*)psi_d;
   const size_t vb = (size_t)n_orb * c->n_int * sizeof(double2);
   if (!c->d_psi_half) {

@@ -75,30 +75,37 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
   const long long n_elem = (long long)g.nx * g.ny * g.nz;
   __syncthreads();
 
-  T fx = T(0), fy = T(0), fz = T(0);
+  T fx = from_d<T>(0.0), fy = from_d<T>(0.0), fz = from_d<T>(0.0);
   T vx[P1];
 #pragma unroll
-  for (int q = 0; q < P1; ++q) vx[q] = T(0);
+  for (int q = 0; q < P1; ++q) vx[q] = from_d<T>(0.0);
   if (valid) {
     const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
     const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
     const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
     const double J = 0.125 * hx * hy * hz;
-    const double wl = (double)sw[u] * (double)sw[v];
-    fx = T(hy * hz / (4.0 * hx) * wl);
-    fy = T(hx * hz / (4.0 * hy) * wl);
-    fz = T(hx * hy / (4.0 * hz) * wl);
+    const double wl = to_d(sw[u]) * to_d(sw[v]);
+    fx = from_d<T>(hy * hz / (4.0 * hx) * wl);
+    fy = from_d<T>(hx * hz / (4.0 * hy) * wl);
+    fz = from_d<T>(hx * hy / (4.0 * hz) * wl);
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
     const double* vp = vks + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
 #pragma unroll
-    for (int q = 0; q < P1; ++q) vx[q] = T(vp[q] * J * wl * (double)sw[q]);
+    for (int q = 0; q < P1; ++q) vx[q] = from_d<T>(vp[q] * J * wl * to_d(sw[q]));
   }
   const long long plane = (long long)g.nix * g.niy;
-  // gather: z-column (a = u, b = v)
+  // gather: z-column (a = u, b = v); Loewdin scales of the column (once per CTA)
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  constexpr bool kDF = std::is_same<T, Df>::value;
   const int Ig = ex * g.p + u, Jg = ey * g.p + v;
   const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
-  const double sG = inG ? g.s[0][Ig] * g.s[1][Jg] : 0.0;
   const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
+  T gsc[P1];
+#pragma unroll
+  for (int c = 0; c < P1; ++c) {
+    const int K = ez * g.p + c;
+    gsc[c] = from_d<T>((inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0);
+  }
 
   for (int oo = 0; oo < orb_per_cta; ++oo) {
     const int o = blockIdx.y * orb_per_cta + oo;
@@ -110,15 +117,28 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
     }
     const double2* in = a.in_base + (long long)o * a.in_stride;
     V col[P1], t[P1];
+    T scT;
+    if constexpr (kF32) scT = d2f_bits(sc);
+    else scT = from_d<T>(sc);
 #pragma unroll
     for (int c = 0; c < P1; ++c) {
       const int K = ez * g.p + c;
       vzero(col[c]);
       if (inG && K >= 1 && K <= g.niz) {
-        const double f = sG * g.s[2][K] * sc;
         const double2 w2 = in[baseG + plane * (K - 1)];
-        col[c].re = T(w2.x * f);
-        col[c].im = T(w2.y * f);
+        if constexpr (kF32) {   // no FP64 arithmetic in the FP32 path
+          const float f = gsc[c] * scT;
+          col[c].re = d2f_bits(w2.x) * f;
+          col[c].im = d2f_bits(w2.y) * f;
+        } else if constexpr (kDF) {   // split on the integer pipe, products in DF64
+          const Df f = df_mul(gsc[c], scT);
+          col[c].re = df_mul(d2df_bits(w2.x), f);
+          col[c].im = df_mul(d2df_bits(w2.y), f);
+        } else {
+          const double f = gsc[c] * sc;
+          col[c].re = w2.x * f;
+          col[c].im = w2.y * f;
+        }
       }
     }
     // forward z, y, x
@@ -155,14 +175,18 @@ __global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
     // z-line (qx = u, qy = v): r = R + cz W W (Kq U)_z
     load_line(col, S1 + v * P1 + u, P2);
     cs_apply<P1>(sK, col, t);
-    double apart = 0.0;
+    T apt = from_d<T>(0.0);
 #pragma unroll
     for (int q = 0; q < P1; ++q) {
       V r = S2[q * P2 + v * P1 + u];
       madd(r, fz, t[q]);
       uq[q] = r;
-      apart += (double)col[q].re * (double)r.re + (double)col[q].im * (double)r.im;
+      dot_acc(apt, col[q], r);
     }
+    double apart;
+    if constexpr (kF32) apart = f2d_bits(apt);
+    else if constexpr (kDF) apart = f2d_bits(apt.hi) + f2d_bits(apt.lo);
+    else apart = apt;
     __syncthreads();
     // backward z, y, x
     cs_apply<P1>(sBT, uq, t);
@@ -242,6 +266,8 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
   const double2* qj = a.in_base + (long long)o * a.in_stride;
   const double2* qm = a.vm_base ? a.vm_base + (long long)o * a.vm_stride : nullptr;
   double2* out = a.out_base + (long long)o * a.out_stride;
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  constexpr bool kDF = std::is_same<T, Df>::value;
   const int rows = g.niy * g.niz;
   double acc = 0.0;
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
@@ -250,21 +276,42 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
     const int ny = node_elems(J, g.p, g.ny, ey, by);
     const int nz = node_elems(K, g.p, g.nz, ez, bz);
     const double syz = g.s[1][J] * g.s[2][K];
+    const float syzf = g.sf[1][J] * g.sf[2][K];
     const long long rowbase = (long long)g.nix * (r);
     for (int I = threadIdx.x + 1; I <= g.nix; I += blockDim.x) {
       const int nx = node_elems(I, g.p, g.nx, ex, bx);
       double re = 0.0, im = 0.0;
+      float fre = 0.f, fim = 0.f;
+      Df dre{0.f, 0.f}, dim{0.f, 0.f};
       for (int kz = 0; kz < nz; ++kz)
         for (int ky = 0; ky < ny; ++ky)
           for (int kx = 0; kx < nx; ++kx) {
             const long long e = ex[kx] + (long long)g.nx * (ey[ky] + (long long)g.ny * ez[kz]);
             const Cx<T> c = evo[e * P3 + bz[kz] * P2 + by[ky] * P1 + bx[kx]];
-            re += (double)c.re;
-            im += (double)c.im;
+            if constexpr (kF32) {
+              fre += c.re;
+              fim += c.im;
+            } else if constexpr (kDF) {
+              dre = df_add(dre, c.re);
+              dim = df_add(dim, c.im);
+            } else {
+              re += c.re;
+              im += c.im;
+            }
           }
-      const double f = g.s[0][I] * syz;
+      if constexpr (kDF) {
+        re = f2d_bits(dre.hi) + f2d_bits(dre.lo);
+        im = f2d_bits(dim.hi) + f2d_bits(dim.lo);
+      }
       const long long idx = rowbase + (I - 1);
-      double2 w = make_double2(f * re, f * im);
+      double2 w;
+      if constexpr (kF32) {   // sum, scale and convert without the FP64 pipe
+        const float f = g.sf[0][I] * syzf;
+        w = make_double2(f2d_bits(f * fre), f2d_bits(f * fim));
+      } else {
+        const double f = g.s[0][I] * syz;
+        w = make_double2(f * re, f * im);
+      }
       if (a.lanczos) {
         const double2 x = qj[idx];
         w.x = fma(-ca, x.x, w.x);
@@ -606,7 +653,9 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   int opc = 1;
   while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
   const int ochunks = (a.n_orb + opc - 1) / opc;
-  const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab : (const T*)c->d_tabf;
+  const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab
+                 : std::is_same<T, float>::value ? (const T*)c->d_tabf
+                                                 : (const T*)c->d_tabdf;
   const Geom g = tdks_geom(c);
   k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
   if (a.lanczos && a.kry && a.part)
@@ -724,6 +773,8 @@ int assemble_blocks(const tdks_ctx* c, int n_orb) {
 tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec) {
   if (prec == TDKS_FP32) {
     TDKS_DISPATCH(c->P1, (hbar_t<P1, float>(c, a)));
+  } else if (prec == TDKS_DF64) {
+    TDKS_DISPATCH(c->P1, (hbar_t<P1, Df>(c, a)));
   } else {
     TDKS_DISPATCH(c->P1, (hbar_t<P1, double>(c, a)));
   }

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -20,8 +21,48 @@ struct Cx {
   T re, im;
 };
 
+// ---- conversions between double and float without the FP64 pipe ------------
+// On GB300 the FP64 unit also executes double<->float conversions at the FP64
+// rate; these bit-level versions run on the integer pipe instead.
+// double -> float, round to nearest even; |x| below FLT_MIN flushes to signed 0.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int E = (int)((hw >> 20) & 0x7ffu);
+  int ef = E - 1023 + 127;
+  if (E == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hw & 0xfffffu) | lw) ? 0x400000u : 0u));
+  if (ef <= 0) return __uint_as_float(sign);
+  unsigned m = ((hw & 0xfffffu) << 3) | (lw >> 29);       // top 23 mantissa bits
+  const unsigned rest = lw & 0x1fffffffu;                  // 29 bits below them
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) {
+    if (++m == 0x800000u) {
+      m = 0;
+      ++ef;
+    }
+  }
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)ef << 23) | m);
+}
+
+// float -> double (exact); float subnormals flush to signed 0.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+  unsigned hw;
+  if (e == 0xffu)
+    hw = sign | 0x7ff00000u | ((u & 0x7fffffu) >> 3) | ((u & 0x7fffffu) ? 0x80000u : 0u);
+  else
+    hw = sign | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lw = (u & 0x7u) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hw << 32) | lw));
+}
+
 template <typename T>
 __device__ __forceinline__ void vzero(T& v) { v = T(0); }
+__device__ __forceinline__ void vzero(Df& v) { v = Df{0.0f, 0.0f}; }
 template <typename T>
 __device__ __forceinline__ void vzero(Cx<T>& v) { v.re = T(0); v.im = T(0); }
 
@@ -42,6 +83,44 @@ template <typename T>
 __device__ __forceinline__ Cx<T> vsub(const Cx<T>& a, const Cx<T>& b) { return Cx<T>{a.re - b.re, a.im - b.im}; }
 template <typename T>
 __device__ __forceinline__ T vscale(T c, const T& v) { return c * v; }
+
+// ---- double-float overloads ------------------------------------------------
+__device__ __forceinline__ void vzero(Cx<Df>& v) { v.re = Df{0.0f, 0.0f}; v.im = Df{0.0f, 0.0f}; }
+__device__ __forceinline__ Cx<Df> vadd(const Cx<Df>& a, const Cx<Df>& b) {
+  return Cx<Df>{df_add(a.re, b.re), df_add(a.im, b.im)};
+}
+__device__ __forceinline__ Cx<Df> vsub(const Cx<Df>& a, const Cx<Df>& b) {
+  return Cx<Df>{df_sub(a.re, b.re), df_sub(a.im, b.im)};
+}
+__device__ __forceinline__ void madd(Cx<Df>& acc, Df c, const Cx<Df>& v) {
+  df_madd(acc.re, c, v.re);
+  df_madd(acc.im, c, v.im);
+}
+__device__ __forceinline__ Cx<Df> vscale(Df c, const Cx<Df>& v) {
+  return Cx<Df>{df_mul(c, v.re), df_mul(c, v.im)};
+}
+
+// scalar conversions used in set-up code (not in the inner loops)
+template <typename T>
+__device__ __forceinline__ T from_d(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ Df from_d<Df>(double x) {
+  const float h = (float)x;
+  return Df{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(Df x) { return (double)x.hi + (double)x.lo; }
+
+// acc += Re(conj(a) b)
+template <typename T>
+__device__ __forceinline__ void dot_acc(T& acc, const Cx<T>& a, const Cx<T>& b) {
+  acc = fma(a.re, b.re, fma(a.im, b.im, acc));
+}
+__device__ __forceinline__ void dot_acc(Df& acc, const Cx<Df>& a, const Cx<Df>& b) {
+  df_madd(acc, a.re, b.re);
+  df_madd(acc, a.im, b.im);
+}
 template <typename T>
 __device__ __forceinline__ Cx<T> vscale(T c, const Cx<T>& v) { return Cx<T>{c * v.re, c * v.im}; }
 

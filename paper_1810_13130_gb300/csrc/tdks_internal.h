@@ -51,6 +51,7 @@ struct Geom {
   int nix, niy, niz;           // interior nodes per axis
   const double* brk[3];        // breakpoints per axis (n+1)
   const double* s[3];          // 1-D factors of M^-1/2 per full node index
+  const float* sf[3];          // the same factors rounded to float
   const double* gauss;         // Gauss points on [-1, 1] (P1)
 };
 
@@ -70,11 +71,13 @@ struct tdks_ctx {
   // device mesh data
   double* d_brk[3] = {nullptr, nullptr, nullptr};
   double* d_s[3] = {nullptr, nullptr, nullptr};          // M^-1/2 1-D factors
+  float* d_sf[3] = {nullptr, nullptr, nullptr};          // float copies
   double* d_coord[3] = {nullptr, nullptr, nullptr};      // node coordinates
   double* d_kd[3] = {nullptr, nullptr, nullptr};         // sum K1_aa / h  (Jacobi diagonal)
   double* d_md[3] = {nullptr, nullptr, nullptr};         // sum h Mg_aa
   double* d_tab = nullptr;     // double tables (layout in tables.cpp)
   float* d_tabf = nullptr;     // float copy
+  float* d_tabdf = nullptr;    // double-float copy (hi, lo pairs)
   double* d_occ = nullptr;
   double* d_R = nullptr;
   double* d_Z = nullptr;

@@ -104,6 +104,20 @@ def test_apply_H_fp32_error_vs_fp64_oracle():
     assert 1e-9 < err < 1e-5
 
 
+@pytest.mark.parametrize("p,n", [(3, (3, 2, 2)), (6, (3, 2, 2)), (8, (2, 2, 1))])
+def test_apply_H_df64_matches_fp64_oracle(p, n):
+    """Double-float contractions: FP64-level agreement (~48-bit arithmetic)."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(*n, p=p, n_orb=2, graded=True)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    psi = synth.random_psi(2, m.N_int, seed=30 + p)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=40 + p).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    got = ctx.apply_H(_cuda(psi), prec=tdks.DF64).cpu().numpy()
+    assert _rel(got, ham.apply_H(m, v, psi)) < 1e-11
+
+
 @pytest.mark.parametrize("precond", [0, 1])
 def test_fields_match_oracle(precond):
     cfg = synth.small_config(3, 2, 2, p=4, n_orb=2, nuc_kind="erf", graded=True)
@@ -213,6 +227,21 @@ def test_magnus_steps_atom_workload():
         assert st["k_full_max"] == max(max(k) for k in info["k_full"])
         assert _rel(g.cpu().numpy(), ref) < 1e-10
         assert abs(st["dipole"][2] - dref[2]) < 1e-10 * abs(dref[2] - d0[2]) + 1e-13
+
+
+def test_magnus_steps_atom_workload_df64():
+    from paper_1810_13130_gb300 import tdks
+    cfg, m, psi0 = _atom_initial_state()
+    ctx = _ctx(cfg)
+    prop = Propagator.from_config(cfg, m)
+    prop.init(psi0)
+    g = _cuda(psi0)
+    ctx.init_propagation(g)
+    ref = psi0
+    for n in range(3):
+        ref, dref, info = prop.magnus_step(ref, cfg.dt)
+        st = ctx.magnus_step(g, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=tdks.DF64)
+        assert _rel(g.cpu().numpy(), ref) < 1e-10
 
 
 def test_magnus_step_with_field_small_system():
