@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false",
+                    help="skip the FP32 / DF64 comparison runs")
     ap.add_argument("--apply-only", action="store_true",
                     help="time standalone Hbar applications (16 orbitals) instead of steps")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -212,6 +214,62 @@ def profile_traffic(prec: str):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def _run_steps(tdks, torch, cfg, prec, steps, warmup, local_rank, psi0, dist=None, timing=True):
+    """K timed Magnus steps of a fresh context from psi0 (kicked on the device)."""
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_cg(1e-10)
+    psi = torch.from_numpy(psi0).cuda()
+    ctx.kick(psi, cfg.kick, cfg.kick_dir)
+    ctx.init_propagation(psi)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ctx.magnus_step(psi, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=prec)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.get_counters(reset=True)
+    ctx.set_timing(timing)
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for _ in range(steps):
+            stats.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if dist:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    cnt = ctx.get_counters(reset=True)
+    ctx.set_timing(False)
+    return ctx, psi, t, stats, cnt, clk.summary()
+
+
+def _atom_dipoles(tdks, torch, prec):
+    """Dipole series of the 2-electron atom workload (oracle ground state, kick
+    1e-3 along z, 100 steps of dt 0.05)."""
+    import numpy as np
+    import synth
+    cfg = synth.config1()
+    gs = np.load(os.path.join(ROOT, "tests", "golden", f"gs_{cfg.name}.npz"))
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_cg(1e-12)
+    g = torch.from_numpy(gs["psibar"].astype(complex)).cuda()
+    ctx.kick(g, cfg.kick, cfg.kick_dir)
+    d = [ctx.init_propagation(g)]
+    for _ in range(cfg.n_steps):
+        d.append(ctx.magnus_step(g, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=prec)["dipole"])
+    ctx.close()
+    return np.array(d)
+
+
 def ours(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -223,43 +281,13 @@ def ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = {"fp64": tdks.FP64, "fp32": tdks.FP32, "df64": tdks.DF64}[args.prec]
+    precs = {"fp64": tdks.FP64, "fp32": tdks.FP32, "df64": tdks.DF64}
+    prec = precs[args.prec]
     cfg = synth.config2()
-    ctx = tdks.Context.from_config(cfg)
-    ctx.set_cg(1e-10)
     psi0 = synth.smooth_orbitals(tuple(n * cfg.p - 1 for n in (cfg.nx, cfg.ny, cfg.nz)),
                                  cfg.n_orb, seed=1)
-    psi = torch.from_numpy(psi0).cuda()
-    ctx.kick(psi, cfg.kick, cfg.kick_dir)
-    ctx.init_propagation(psi)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        return ctx.magnus_step(psi, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=prec)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ctx.get_counters(reset=True)
-    ctx.set_timing(True)
-    stats = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        torch.cuda.nvtx.range_push("timed")
-        ev0.record(stream)
-        for _ in range(args.steps):
-            stats.append(step())
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    if dist:
-        dist.barrier()
-    t = ev0.elapsed_time(ev1) * 1e-3
-    cnt = ctx.get_counters(reset=True)
-    ctx.set_timing(False)
+    ctx, psi, t, stats, cnt, clocks = _run_steps(tdks, torch, cfg, prec, args.steps, args.warmup,
+                                                 local_rank, psi0, dist)
     if dist:
         tt = torch.tensor([t], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -268,7 +296,7 @@ def ours(args, rank: int, world: int, local_rank: int):
     applies = sum(s["applies"] for s in stats)
     value = world * cfg.n_orb * args.steps / t
     hpsi = world * n_int * applies / t / 1e9
-    # roofline of the dominant kernel (Hbar colour launches, timed inside the region)
+    # roofline of the dominant kernel (the Hbar element kernel, timed inside the region)
     P1 = cfg.p + 1
     flops_unit = 36 * P1 ** 4 + 24 * P1 ** 3
     apply_s = cnt["apply_ms"] * 1e-3
@@ -303,7 +331,7 @@ def ours(args, rank: int, world: int, local_rank: int):
                        "k_full_max": max(s["k_full_max"] for s in stats),
                        "substeps": sum(s["substeps"] for s in stats),
                        "cg_iters_per_solve": statistics.mean(c for s in stats for c in s["cg_iters"])},
-            "roofline": roofline, "gpu_launches": cnt["launches"], "clocks": clk.summary()}
+            "roofline": roofline, "gpu_launches": cnt["launches"], "clocks": clocks}
     # end to end through the public C-ABI with host buffers (pinned), every step:
     # H2D of the orbitals + field, the step, D2H of the orbitals + dipole
     if args.e2e_steps > 0:
@@ -321,6 +349,25 @@ def ours(args, rank: int, world: int, local_rank: int):
         line["e2e"] = {"value": world * cfg.n_orb * args.e2e_steps / te, "unit": "orbital-steps/s",
                        "h2d_bytes_per_step": nb + 48, "d2h_bytes_per_step": nb + 24,
                        "steps": args.e2e_steps}
+    ctx.close()
+    # mixed precision: same workload and step count per contraction type; dipole
+    # error on the atom workload against the FP64 path, relative to the largest
+    # induced dipole |d(t) - d(0)| over 100 steps
+    if args.mixed and args.prec == "fp64":
+        d64 = _atom_dipoles(tdks, torch, tdks.FP64)
+        ind = float(np.abs(d64[:, 2] - d64[0, 2]).max())
+        mixed = {"dipole_err_workload": "atom_soft_Z2_6x6x6_p4, oracle ground state, kick 1e-3 z, "
+                                        "100 steps dt 0.05; max |d - d_fp64| / max |d_fp64 - d_fp64(0)|"}
+        for name in ("fp32", "df64"):
+            c2, _, t2, st2, _, _ = _run_steps(tdks, torch, cfg, precs[name], args.steps, args.warmup,
+                                              local_rank, psi0, dist, timing=False)
+            c2.close()
+            v2 = world * cfg.n_orb * args.steps / t2
+            dm = _atom_dipoles(tdks, torch, precs[name])
+            mixed[name] = {"value": v2, "unit": "orbital-steps/s", "ms_per_step": 1e3 * t2 / args.steps,
+                           "speedup_vs_fp64": v2 / value,
+                           "dipole_rel_err": float(np.abs(dm[:, 2] - d64[:, 2]).max() / ind)}
+        line["mixed"] = mixed
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         recs = run_oracle_sample(1)
         st = [r for r in recs if "step" in r]
@@ -329,7 +376,6 @@ def ours(args, rank: int, world: int, local_rank: int):
                                 "timed_sample_s": st[0]["t_sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 

@@ -48,8 +48,10 @@ struct Cfg {
 //   y-line:  R += cy W W (Kq u~)_y;  z-line: r = R + cz W W (Kq u~)_z
 //   backward z -> y -> x (B^T), scatter-add of the x-line with the Loewdin scale.
 // ---------------------------------------------------------------------------
+// Register budget of the element kernel: at most 128 registers, so that two CTAs
+// (16 warps) share an SM.
 template <int P1, typename T>
-__global__ void __launch_bounds__(256) k_hbar(Geom g, const T* __restrict__ tab,
+__global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
                                               int orb_per_cta, Cx<T>* __restrict__ ev) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;

@@ -166,6 +166,95 @@ __device__ __forceinline__ void cs_apply(const T* __restrict__ t, const V (&in)[
   }
 }
 
+// Double-float version: each dot product keeps an unnormalized (hi, err) pair --
+// hi grows by exact two-sums, the rounding errors and product tails accumulate in
+// err -- and is renormalized once, when the output pair is formed.
+struct DfAcc {
+  float hi, err;
+};
+__device__ __forceinline__ DfAcc dfa_first(Df c, Df x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float pe = __fmaf_rn(c.hi, x.hi, -p);
+  pe = __fmaf_rn(c.hi, x.lo, pe);
+  pe = __fmaf_rn(c.lo, x.hi, pe);
+  return DfAcc{p, pe};
+}
+__device__ __forceinline__ void dfa_madd(DfAcc& a, Df c, Df x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float pe = __fmaf_rn(c.hi, x.hi, -p);
+  pe = __fmaf_rn(c.hi, x.lo, pe);
+  pe = __fmaf_rn(c.lo, x.hi, pe);
+  const float s = __fadd_rn(a.hi, p);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  a.err = __fadd_rn(a.err, __fadd_rn(e, pe));
+  a.hi = s;
+}
+// (a + b, a - b) of two accumulators, renormalized
+__device__ __forceinline__ void dfa_pm(const DfAcc& a, const DfAcc& b, Df& plus, Df& minus) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  plus = df_norm(s, __fadd_rn(e, __fadd_rn(a.err, b.err)));
+  s = __fsub_rn(a.hi, b.hi);
+  v = __fsub_rn(s, a.hi);
+  e = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fadd_rn(b.hi, v));
+  minus = df_norm(s, __fadd_rn(e, __fsub_rn(a.err, b.err)));
+}
+
+template <int N>
+__device__ __forceinline__ void cs_apply_df1(const Df* __restrict__ t, const Df (&in)[N], Df (&out)[N]) {
+  constexpr int h = N / 2;
+  constexpr int hh = h > 0 ? h : 1;
+  const Df* Me = t;
+  const Df* Mo = t + h * h;
+  const Df* Mc = t + 2 * h * h;
+  const Df* Mr = Mc + h;
+  Df e[hh], o[hh];
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    e[i] = df_add(in[i], in[N - 1 - i]);
+    o[i] = df_sub(in[i], in[N - 1 - i]);
+  }
+#pragma unroll
+  for (int q = 0; q < h; ++q) {
+    DfAcc a = dfa_first(Me[q * h], e[0]);
+    DfAcc b = dfa_first(Mo[q * h], o[0]);
+#pragma unroll
+    for (int i = 1; i < h; ++i) {
+      dfa_madd(a, Me[q * h + i], e[i]);
+      dfa_madd(b, Mo[q * h + i], o[i]);
+    }
+    if (N & 1) dfa_madd(a, Mc[q], in[h]);
+    dfa_pm(a, b, out[q], out[N - 1 - q]);
+  }
+  if (N & 1) {
+    DfAcc c = dfa_first(Mr[h], in[h]);
+#pragma unroll
+    for (int i = 0; i < h; ++i) dfa_madd(c, Mr[i], e[i]);
+    out[h] = df_norm(c.hi, c.err);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void cs_apply(const Df* __restrict__ t, const Cx<Df> (&in)[N],
+                                         Cx<Df> (&out)[N]) {
+  if constexpr (N == 1) {
+    out[0] = vscale(t[0 + 2 * 0 + 0], in[0]);
+  } else {
+    Df ir[N], ii[N], orr[N], oi[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      ir[i] = in[i].re;
+      ii[i] = in[i].im;
+    }
+    cs_apply_df1<N>(t, ir, orr);
+    cs_apply_df1<N>(t, ii, oi);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = Cx<Df>{orr[i], oi[i]};
+  }
+}
+
 template <int N, typename V>
 __device__ __forceinline__ void load_line(V (&r)[N], const V* src, int stride) {
 #pragma unroll
