@@ -5,8 +5,9 @@ Sec. VI.B, Eqs. 36-38.  For each orbital separately:
     w = Hbar q_j;  alpha_j = Re(q_j^H w);  w -= alpha_j q_j + beta_{j-1} q_{j-1}
     beta_j = ||w||;  T_j = tridiag(beta, alpha, beta)  (Hbar Hermitian -> T real)
     y = exp(-i tau T_j) e_1                 (eigendecomposition of T_j, Eq. 37)
-    eps_j = tau beta_j ||psibar|| |y_j|      (Eq. 38: the (j+1, j) entry of the
-                                            projected -i tau Hbar has modulus tau beta_j)
+    eps_j = |tau| beta_j ||psibar|| |y_j|    (Eq. 38: the (j+1, j) entry of the
+                                            projected -i tau Hbar has modulus |tau| beta_j;
+                                            tau < 0 gives the backward propagator)
     stop when eps_j <= tol:  z = ||psibar|| Q_j y;  otherwise q_{j+1} = w / beta_j.
 The plain three-term recurrence is used (the paper names no re-orthogonalization).
 
@@ -53,7 +54,7 @@ def expm_lanczos(apply_vec, psi: np.ndarray, tau: float, tol: float, k_max: int 
         v = psi[a].astype(complex)
         t_rem = float(tau)
         ks, errs = [], []
-        while t_rem > 0.0:
+        while t_rem != 0.0:
             if len(ks) >= max_sub:
                 raise NotConverged(f"orbital {a}: more than {max_sub} sub-steps")
             nrm = np.linalg.norm(v)
@@ -72,7 +73,7 @@ def expm_lanczos(apply_vec, psi: np.ndarray, tau: float, tol: float, k_max: int 
                 alpha.append(a_j)
                 beta.append(b_j)
                 y = exp_tridiag_e1(alpha, beta[:-1], t_rem)
-                err = t_rem * b_j * nrm * abs(y[-1])
+                err = abs(t_rem) * b_j * nrm * abs(y[-1])
                 stop = (err <= tol) if kf is None else (j + 1 == kf)
                 if stop or b_j == 0.0:
                     v = nrm * (np.array(Q).T @ y)
@@ -90,7 +91,7 @@ def expm_lanczos(apply_vec, psi: np.ndarray, tau: float, tol: float, k_max: int 
             for m in range(1, 64):
                 ts = t_rem / 2.0 ** m
                 y = exp_tridiag_e1(alpha, beta[:-1], ts)
-                err = ts * beta[-1] * nrm * abs(y[-1])
+                err = abs(ts) * beta[-1] * nrm * abs(y[-1])
                 if err <= tol:
                     break
             else:

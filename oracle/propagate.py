@@ -112,8 +112,9 @@ class Propagator:
                             self.tol, self.k_max, k_fixed=k_fixed)
 
     def magnus_step(self, psibar, dt, E_quarter=(0, 0, 0), E_half=(0, 0, 0),
-                    k_fixed=None):
-        """One predictor-corrector Magnus step; returns (psibar^n, dipole^n, info)."""
+                    k_fixed=None, record=False):
+        """One predictor-corrector Magnus step; returns (psibar^n, dipole^n, info).
+        With record=True, info also holds the step's intermediates (for the adjoint)."""
         v_pred = self.v_nuc + 1.25 * self.vhxc_1 - 0.25 * self.vhxc_2 + self.v_field(E_quarter)
         kf1 = None if k_fixed is None else k_fixed[0]
         kf2 = None if k_fixed is None else k_fixed[1]
@@ -124,7 +125,12 @@ class Propagator:
         vhxc_new, rho = self.v_hxc(psi_new)
         self.vhxc_2 = self.vhxc_1
         self.vhxc_1 = vhxc_new
-        return psi_new, ham.dipole(self.mesh, rho), {"k_half": info1["k"], "k_full": info2["k"]}
+        info = {"k_half": info1["k"], "k_full": info2["k"]}
+        if record:
+            info.update(psi_prev=psibar, psi_half=psi_half, psi_new=psi_new, v_pred=v_pred,
+                        v_mid=v_mid, rho_half=ham.density(self.mesh, psi_half, self.occ),
+                        rho_new=rho)
+        return psi_new, ham.dipole(self.mesh, rho), info
 
     def energy(self, psibar, E=(0, 0, 0)):
         """Total energy sum_a f_a <psibar_a|T + V_N + V_field|psibar_a> + E_H + E_xc."""

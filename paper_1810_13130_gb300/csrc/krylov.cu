@@ -244,6 +244,17 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
   return true;
 }
 
+// exp(-i tau T) e_1 for either sign of tau: for tau < 0 it is the complex
+// conjugate of exp(-i |tau| T) e_1 (T and e_1 are real).
+__device__ bool cheb_exp_signed(int m, double tau, ChebWork& W) {
+  const bool ok = cheb_exp(m, fabs(tau), W);
+  if (ok && tau < 0.0) {
+    for (int i = (threadIdx.x & 31); i < m; i += 32) W.yi[i] = -W.yi[i];
+    __syncwarp();
+  }
+  return ok;
+}
+
 // One warp per orbital: beta_j, small exponential, a-posteriori estimate, decision.
 __global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double* npart,
                           int64_t npstride, int nb) {
@@ -267,16 +278,16 @@ __global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double
   if (!isfinite(beta)) {
     decision = -1;
   } else {
-    const bool ok = cheb_exp(m, K.t_rem, W);
-    const double err = ok ? K.t_rem * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
+    const bool ok = cheb_exp_signed(m, K.t_rem, W);
+    const double err = ok ? fabs(K.t_rem) * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
     if (ok && (err <= tol || beta == 0.0)) {
       decision = 1;
     } else if (m >= kmax) {
       decision = -1;
       for (int s = 1; s < 60; ++s) {
         const double ts = ldexp(K.t_rem, -s);
-        const bool ok2 = cheb_exp(m, ts, W);
-        const double e2 = ok2 ? ts * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
+        const bool ok2 = cheb_exp_signed(m, ts, W);
+        const double e2 = ok2 ? fabs(ts) * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
         if (ok2 && e2 <= tol) {
           decision = 2;
           tau_used = ts;
