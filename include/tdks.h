@@ -199,6 +199,39 @@ tdks_status tdks_propagate_host(tdks_ctx* ctx, const double* psi_host_in,
                                 double dt, const double* E_host, double tol, int k_max,
                                 int prec, double* dipole_host);
 
+/* Dipole-response objective and its gradient with respect to the field (the
+ * adjoint of Secs. VI.B and V; the paper optimizes nothing, this is the reverse
+ * mode of its propagation).
+ *
+ * J = sum_{n=0}^{n_steps} w_host[n] (e . mu_n)^2, mu_0 the dipole of psi0 and mu_n
+ * the dipole after Magnus step n with field samples E_host[n-1] ([n_steps][6]:
+ * E(t+dt/4) for the predictor, then E(t+dt/2) for the corrector).
+ *
+ * tdks_objective_forward: psi0 is device memory ([n_orb][n_int] complex, left
+ * unchanged); re-initializes the propagation (as tdks_init_propagation) and
+ * propagates n_steps steps with precision prec, storing a checkpoint of the
+ * state every ckpt_every steps in device memory owned by the context
+ * (ceil(n_steps / ckpt_every) x (orbitals + 2 potentials + Poisson solution)).
+ * Writes J to *J_host and, if dip_host is not NULL, the n_steps + 1 dipoles
+ * ([n_steps+1][3]).  Replaces the state of an earlier forward call.
+ *
+ * tdks_objective_backward: after a forward call, writes dJ/dE to dJdE_host
+ * ([n_steps][6], same layout as E_host).  Each segment of ckpt_every steps is
+ * recomputed from its checkpoint (extra device memory: ckpt_every x (2 orbital
+ * sets + 2 potentials)), then swept in reverse: the exact adjoint of every
+ * exponential (a Lanczos exponential with time -tau), the Frechet derivative of
+ * exp(-i tau Hbar[v]) with respect to v by n_s-point Gauss-Legendre quadrature
+ * in the splitting parameter (1 <= n_s <= 64), and the adjoints of the Hartree
+ * solve (Eq. 19), the LDA potential and the density.  Each adjoint exponential
+ * must converge within one Krylov basis of dimension k_max (else
+ * TDKS_ERR_NOT_CONVERGED).  Leaves the context's propagation state undefined:
+ * call tdks_init_propagation before propagating again.  Synchronizes. */
+tdks_status tdks_objective_forward(tdks_ctx* ctx, const double* psi0, int n_orb, int n_steps,
+                                   double dt, const double* E_host, const double* w_host,
+                                   const double e[3], int ckpt_every, double tol, int k_max,
+                                   int prec, double* J_host, double* dip_host);
+tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
+
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar
  * colour launches, element-orbital applications, and -- when timing is on --
  * the summed device time of the Hbar applications inside tdks_expm measured

@@ -87,8 +87,10 @@ void free_ctx(tdks_ctx* c) {
   cudaFree(c->d_pv);
   cudaFree(c->d_Ap);
   cudaFree(c->d_cg);
-  cudaFree(c->d_V);
-  cudaFree(c->d_kry);
+  for (int w = 0; w < 2; ++w) {
+    cudaFree(c->d_Vw[w]);
+    cudaFree(c->d_kryw[w]);
+  }
   cudaFree(c->d_psi_half);
   cudaFree(c->d_evec);
   cudaFree(c->d_psi_e2e);
@@ -102,6 +104,7 @@ void free_ctx(tdks_ctx* c) {
     cudaFree(c->d_fdmL[d]);
   }
   if (c->h_red) cudaFreeHost(c->h_red);
+  adjoint_free(c);
   if (c->ev[0]) cudaEventDestroy(c->ev[0]);
   if (c->ev[1]) cudaEventDestroy(c->ev[1]);
   delete c;
@@ -297,7 +300,6 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
     if (cudaMemset(*f, 0, c->n_int * sizeof(double)) != cudaSuccess) return fail(TDKS_ERR_CUDA);
   }
   if ((st = dalloc(c, &c->d_cg, 1)) != TDKS_OK) return fail(st);
-  if ((st = dalloc(c, &c->d_kry, (size_t)c->n_orb)) != TDKS_OK) return fail(st);
   const int bpc = hbar_blocks_per_color(c);
   c->part_stride = std::max<int64_t>(2048, 8 * (int64_t)bpc);
   if ((st = dalloc(c, &c->d_part, (size_t)(2 * (c->n_orb + 2) * c->part_stride + 8192))) != TDKS_OK)
@@ -367,7 +369,7 @@ tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb,
   if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
     return tdks_fail(c, TDKS_ERR_ARG, "precision");
   ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0,
-              0, nullptr, 0, nullptr, 0};
+              0, nullptr, 0, nullptr, 0, 0};
   c->n_apply_units += (int64_t)n_orb * c->n_elem;
   return launch_hbar_apply(c, a, prec);
 }
@@ -430,41 +432,8 @@ tdks_status tdks_init_propagation(tdks_ctx* c, const double* psi, int n_orb, dou
 tdks_status tdks_magnus_step(tdks_ctx* c, double* psi_d, int n_orb, double dt, const double Eq[3],
                              const double Eh[3], double tol, int k_max, int prec, tdks_stats* stats) {
   if (!c || !psi_d) return TDKS_ERR_ARG;
-  TDKS_TRY(check_orb(c, n_orb));
-  if (!c->propagation_ready) return tdks_fail(c, TDKS_ERR_ARG, "call tdks_init_propagation first");
-  if (!(dt > 0) || !(tol > 0)) return tdks_fail(c, TDKS_ERR_ARG, "dt > 0 and tol > 0");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
-    return tdks_fail(c, TDKS_ERR_ARG, "precision");
-  double2* psi = (double2*)psi_d;
-  const size_t vb = (size_t)n_orb * c->n_int * sizeof(double2);
-  if (!c->d_psi_half) {
-    TDKS_TRY(dalloc(c, &c->d_psi_half, (size_t)c->n_orb * c->n_int));
-  }
-  tdks_stats st{};
-  int kseen = 0, nsub = 0;
-  int64_t app = 0;
-  // predictor: V(t + dt/4) = V_N + 1.25 V_HXC^{n-1} - 0.25 V_HXC^{n-2} - E(t + dt/4).r
-  TDKS_TRY(launch_combine(c, c->d_vks, c->d_vnuc, 1.25, c->d_vhxc1, -0.25, c->d_vhxc2, nullptr, Eq));
-  TDKS_CU(c, cudaMemcpyAsync(c->d_psi_half, psi, vb, cudaMemcpyDeviceToDevice, c->stream));
-  TDKS_TRY(run_expm(c, c->d_psi_half, c->d_psi_half, n_orb, 0.5 * dt, tol, k_max, prec, nullptr,
-                    &kseen, &app, &nsub));
-  st.k_half_max = kseen;
-  st.applies += app;
-  st.substeps += nsub;
-  // corrector: V(t + dt/2) from the density of psi^{n-1/2}
-  TDKS_TRY(vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[0]));
-  // d_vtmp now holds V_HXC(t + dt/2) (vhxc_of used d_vtmp as scratch before writing it)
-  TDKS_TRY(launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, Eh));
-  TDKS_TRY(run_expm(c, psi, psi, n_orb, dt, tol, k_max, prec, nullptr, &kseen, &app, &nsub));
-  st.k_full_max = kseen;
-  st.applies += app;
-  st.substeps += nsub;
-  // history: V_HXC^{n-2} <- V_HXC^{n-1}, V_HXC^{n-1} <- V_HXC[rho(psi^n)]
-  std::swap(c->d_vhxc1, c->d_vhxc2);
-  TDKS_TRY(vhxc_of(c, psi, n_orb, c->d_vhxc1, &st.cg_iters[1]));
-  TDKS_TRY(run_dipole(c, c->d_rho, st.dipole));
-  if (stats) *stats = st;
-  return TDKS_OK;
+  return magnus_step_impl(c, (double2*)psi_d, n_orb, dt, Eq, Eh, tol, k_max, prec, stats, nullptr,
+                          nullptr, nullptr);
 }
 
 tdks_status tdks_propagate_host(tdks_ctx* c, const double* psi_in, double* psi_out, int n_orb,
@@ -513,3 +482,47 @@ tdks_status tdks_get_counters(tdks_ctx* c, tdks_counters* out, int reset) {
 }
 
 }  // extern "C"
+
+tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, const double Eq[3],
+                             const double Eh[3], double tol, int k_max, int prec, tdks_stats* stats,
+                             double2* keep_half, double* keep_vpred, double* keep_vmid) {
+  TDKS_TRY(check_orb(c, n_orb));
+  if (!c->propagation_ready) return tdks_fail(c, TDKS_ERR_ARG, "call tdks_init_propagation first");
+  if (!(dt > 0) || !(tol > 0)) return tdks_fail(c, TDKS_ERR_ARG, "dt > 0 and tol > 0");
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+    return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  const size_t vb = (size_t)n_orb * c->n_int * sizeof(double2);
+  const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
+  if (!c->d_psi_half) {
+    TDKS_TRY(dalloc(c, &c->d_psi_half, (size_t)c->n_orb * c->n_int));
+  }
+  tdks_stats st{};
+  int kseen = 0, nsub = 0;
+  int64_t app = 0;
+  // predictor: V(t + dt/4) = V_N + 1.25 V_HXC^{n-1} - 0.25 V_HXC^{n-2} - E(t + dt/4).r
+  TDKS_TRY(launch_combine(c, c->d_vks, c->d_vnuc, 1.25, c->d_vhxc1, -0.25, c->d_vhxc2, nullptr, Eq));
+  if (keep_vpred) TDKS_CU(c, cudaMemcpyAsync(keep_vpred, c->d_vks, fb, cudaMemcpyDeviceToDevice, c->stream));
+  TDKS_CU(c, cudaMemcpyAsync(c->d_psi_half, psi, vb, cudaMemcpyDeviceToDevice, c->stream));
+  TDKS_TRY(run_expm(c, c->d_psi_half, c->d_psi_half, n_orb, 0.5 * dt, tol, k_max, prec, nullptr,
+                    &kseen, &app, &nsub));
+  if (keep_half) TDKS_CU(c, cudaMemcpyAsync(keep_half, c->d_psi_half, vb, cudaMemcpyDeviceToDevice, c->stream));
+  st.k_half_max = kseen;
+  st.applies += app;
+  st.substeps += nsub;
+  // corrector: V(t + dt/2) from the density of psi^{n-1/2}
+  TDKS_TRY(vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[0]));
+  // d_vtmp now holds V_HXC(t + dt/2) (vhxc_of used d_vtmp as scratch before writing it)
+  TDKS_TRY(launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, Eh));
+  if (keep_vmid) TDKS_CU(c, cudaMemcpyAsync(keep_vmid, c->d_vks, fb, cudaMemcpyDeviceToDevice, c->stream));
+  TDKS_TRY(run_expm(c, psi, psi, n_orb, dt, tol, k_max, prec, nullptr, &kseen, &app, &nsub));
+  st.k_full_max = kseen;
+  st.applies += app;
+  st.substeps += nsub;
+  // history: V_HXC^{n-2} <- V_HXC^{n-1}, V_HXC^{n-1} <- V_HXC[rho(psi^n)]
+  std::swap(c->d_vhxc1, c->d_vhxc2);
+  TDKS_TRY(vhxc_of(c, psi, n_orb, c->d_vhxc1, &st.cg_iters[1]));
+  TDKS_TRY(run_dipole(c, c->d_rho, st.dipole));
+  if (stats) *stats = st;
+  return TDKS_OK;
+}
+

@@ -325,6 +325,11 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
         }
         acc = fma(w.x, w.x, fma(w.y, w.y, acc));
       }
+      if (a.accumulate) {
+        const double2 o2 = out[idx];
+        w.x += o2.x;
+        w.y += o2.y;
+      }
       out[idx] = w;
     }
   }
@@ -448,7 +453,8 @@ __global__ void __launch_bounds__(256) k_stiff(Geom g, const double* __restrict_
 template <int P1>
 __global__ void __launch_bounds__(256) k_load(Geom g, const double* __restrict__ tab,
                                               const double* __restrict__ fq,
-                                              double* __restrict__ out, double scale, int color) {
+                                              double* __restrict__ out, double scale, int color,
+                                              int weighted) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -471,11 +477,11 @@ __global__ void __launch_bounds__(256) k_load(Geom g, const double* __restrict__
     const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
     const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
     const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
-    const double Jw = 0.125 * hx * hy * hz * scale * sw[u] * sw[v];
+    const double Jw = weighted ? 0.125 * hx * hy * hz * scale * sw[u] * sw[v] : scale;
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
     const double* fp = fq + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
 #pragma unroll
-    for (int q = 0; q < P1; ++q) col[q] = fp[q] * Jw * sw[q];
+    for (int q = 0; q < P1; ++q) col[q] = fp[q] * Jw * (weighted ? sw[q] : 1.0);
   }
   cs_apply<P1>(sBT, col, t);
   store_line(t, S1 + v * P2 + u * P1, 1);                 // [qz][qy][a]
@@ -521,7 +527,8 @@ __device__ __forceinline__ void forward_lines(V (&col)[P1], V (&uq)[P1], V* S1, 
 template <int P1>
 __global__ void __launch_bounds__(256) k_interp(Geom g, const double* __restrict__ tab,
                                                 const double* __restrict__ nodal,
-                                                double* __restrict__ fq) {
+                                                double* __restrict__ fq, double scale,
+                                                int weighted) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -548,6 +555,17 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const double* __restrict
   forward_lines<P1, double, double>(col, uq, S1, S2, sB, u, v);
   if (valid) {
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
+    double f = scale;
+    if (weighted) {
+      const double* w = tab + tab_off_w(P1);
+      f *= 0.125 * (g.brk[0][ex + 1] - g.brk[0][ex]) * (g.brk[1][ey + 1] - g.brk[1][ey]) *
+           (g.brk[2][ez + 1] - g.brk[2][ez]) * w[u] * w[v];
+#pragma unroll
+      for (int q = 0; q < P1; ++q) uq[q] *= f * w[q];
+    } else if (f != 1.0) {
+#pragma unroll
+      for (int q = 0; q < P1; ++q) uq[q] *= f;
+    }
     store_line(uq, fq + e * P3 + v * P2 + u * P1, 1);
   }
 }
@@ -606,6 +624,143 @@ __global__ void __launch_bounds__(256) k_density(Geom g, const double* __restric
   if (valid) {
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
     store_line(acc, rho + e * P3 + v * P2 + u * P1, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Density adjoint: element-local (B^T)^(x)3 [2 occ_a g_rho psi_a(x_q)] for every
+// orbital (the assembly and the Loewdin scale follow in k_assemble).
+// ---------------------------------------------------------------------------
+template <int P1>
+__global__ void __launch_bounds__(256) k_dens_adj(Geom g, const double* __restrict__ tab,
+                                                  const double2* __restrict__ psi, int64_t stride,
+                                                  int n_orb, const double* __restrict__ occ,
+                                                  const double* __restrict__ grho,
+                                                  Cx<double>* __restrict__ ev) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  typedef Cx<double> V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* sB = reinterpret_cast<double*>(smem);
+  double* sBT = sB + CS;
+  const size_t off = (2 * CS * sizeof(double) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  V* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < 2 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
+  int ex = 0, ey = 0, ez = 0;
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const bool valid = plain_elem(g, eidx, ex, ey, ez);
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  __syncthreads();
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
+  const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
+  const double sxy = inIJ ? g.s[0][I] * g.s[1][Jn] : 0.0;
+  const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
+  const long long plane = (long long)g.nix * g.niy;
+  double gx[P1];
+#pragma unroll
+  for (int q = 0; q < P1; ++q) gx[q] = valid ? grho[eidx * P3 + v * P2 + u * P1 + q] : 0.0;
+  for (int o = 0; o < n_orb; ++o) {
+    const double2* in = psi + (long long)o * stride;
+    V col[P1], uq[P1], t[P1];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      const int K = ez * g.p + c;
+      vzero(col[c]);
+      if (inIJ && K >= 1 && K <= g.niz) {
+        const double f = sxy * g.s[2][K];
+        const double2 w2 = in[base + plane * (K - 1)];
+        col[c].re = w2.x * f;
+        col[c].im = w2.y * f;
+      }
+    }
+    forward_lines<P1, V, double>(col, uq, S1, S2, sB, u, v);
+    const double f2 = 2.0 * occ[o];
+#pragma unroll
+    for (int q = 0; q < P1; ++q) uq[q] = vscale(f2 * gx[q], uq[q]);
+    __syncthreads();                                       // S1/S2 free again
+    cs_apply<P1>(sBT, uq, t);                              // x-line -> B^T along x
+    store_line(t, S1 + v * P2 + u * P1, 1);                // [qz][qy][a]
+    __syncthreads();
+    load_line(col, S1 + v * P2 + u, P1);                   // y-line (a = u, qz = v)
+    cs_apply<P1>(sBT, col, t);
+    store_line(t, S2 + v * P2 + u, P1);                    // [qz][b][a]
+    __syncthreads();
+    load_line(col, S2 + v * P1 + u, P2);                   // z-line (a = u, b = v)
+    cs_apply<P1>(sBT, col, t);
+    if (valid) store_line(t, ev + ((long long)o * n_elem + eidx) * P3 + v * P1 + u, P2);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// g_q += coef wJ_q sum_a Im(conj(mu_a(x_q)) phi_a(x_q))   (Frechet term of the
+// exponential with respect to the potential at the Gauss points)
+// ---------------------------------------------------------------------------
+template <int P1>
+__global__ void __launch_bounds__(256) k_cross(Geom g, const double* __restrict__ tab,
+                                               const double2* __restrict__ mu,
+                                               const double2* __restrict__ phi, int64_t stride,
+                                               int n_orb, double coef, double* __restrict__ gq) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  typedef Cx<double> V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* sB = reinterpret_cast<double*>(smem);
+  double* sw = sB + CS;
+  const size_t off = ((CS + P1) * sizeof(double) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  V* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
+  int ex = 0, ey = 0, ez = 0;
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const bool valid = plain_elem(g, eidx, ex, ey, ez);
+  __syncthreads();
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
+  const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
+  const double sxy = inIJ ? g.s[0][I] * g.s[1][Jn] : 0.0;
+  const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
+  const long long plane = (long long)g.nix * g.niy;
+  double acc[P1];
+#pragma unroll
+  for (int q = 0; q < P1; ++q) acc[q] = 0.0;
+  for (int o = 0; o < n_orb; ++o) {
+    V cm[P1], cp[P1], mq[P1], pq[P1];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      const int K = ez * g.p + c;
+      vzero(cm[c]);
+      vzero(cp[c]);
+      if (inIJ && K >= 1 && K <= g.niz) {
+        const double f = sxy * g.s[2][K];
+        const long long idx = (long long)o * stride + base + plane * (K - 1);
+        const double2 a = mu[idx], b = phi[idx];
+        cm[c].re = a.x * f;
+        cm[c].im = a.y * f;
+        cp[c].re = b.x * f;
+        cp[c].im = b.y * f;
+      }
+    }
+    forward_lines<P1, V, double>(cm, mq, S1, S2, sB, u, v);
+    __syncthreads();
+    forward_lines<P1, V, double>(cp, pq, S1, S2, sB, u, v);
+#pragma unroll
+    for (int q = 0; q < P1; ++q) acc[q] += mq[q].re * pq[q].im - mq[q].im * pq[q].re;
+    __syncthreads();
+  }
+  if (valid) {
+    const double J = 0.125 * (g.brk[0][ex + 1] - g.brk[0][ex]) * (g.brk[1][ey + 1] - g.brk[1][ey]) *
+                     (g.brk[2][ez + 1] - g.brk[2][ez]);
+    double* gp = gq + eidx * P3 + v * P2 + u * P1;
+#pragma unroll
+    for (int q = 0; q < P1; ++q) gp[q] += coef * J * sw[u] * sw[v] * sw[q] * acc[q];
   }
 }
 
@@ -686,7 +841,7 @@ tdks_status stiff_t(tdks_ctx* c, const double* in, double* out, double* part, co
 }
 
 template <int P1>
-tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale) {
+tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale, int weighted) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   const size_t smem = (CS + P1 + (size_t)E * 2 * P3) * sizeof(double);
@@ -694,20 +849,20 @@ tdks_status load_t(tdks_ctx* c, const double* fq, double* out, double scale) {
   dim3 block(P2, E), grid(blocks_per_color_t<P1>(c));
   const Geom g = tdks_geom(c);
   for (int color = 0; color < 8; ++color)
-    k_load<P1><<<grid, block, smem, c->stream>>>(g, c->d_tab, fq, out, scale, color);
+    k_load<P1><<<grid, block, smem, c->stream>>>(g, c->d_tab, fq, out, scale, color, weighted);
   c->n_launch += 8;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
 }
 
 template <int P1>
-tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq) {
+tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq, double scale, int weighted) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   const size_t smem = (CS + (size_t)E * 2 * P3) * sizeof(double);
   TDKS_CU(c, set_smem(k_interp<P1>, smem));
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
-  k_interp<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, nodal, fq);
+  k_interp<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, nodal, fq, scale, weighted);
   c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
@@ -741,6 +896,50 @@ tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho) {
   }
 
 }  // namespace
+
+template <int P1>
+tdks_status dens_adj_t(tdks_ctx* c, const double2* psi, int n_orb, const double* grho, double2* lam,
+                       int accumulate) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = ((2 * CS * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
+  TDKS_CU(c, set_smem(k_dens_adj<P1>, smem));
+  const size_t need = (size_t)n_orb * c->n_elem * P3 * sizeof(Cx<double>);
+  if (need > c->evec_bytes) {
+    cudaFree(c->d_evec);
+    c->d_evec = nullptr;
+    c->evec_bytes = 0;
+    if (cudaMalloc(&c->d_evec, need) != cudaSuccess) {
+      cudaGetLastError();
+      return tdks_fail(c, TDKS_ERR_NOMEM, "element-result buffer");
+    }
+    c->evec_bytes = need;
+  }
+  Cx<double>* ev = static_cast<Cx<double>*>(c->d_evec);
+  const Geom g = tdks_geom(c);
+  k_dens_adj<P1><<<dim3(elem_blocks_t<P1>(c)), dim3(P2, E), smem, c->stream>>>(
+      g, c->d_tab, psi, c->n_int, n_orb, c->d_occ, grho, ev);
+  ApplyArgs a{psi, c->n_int, lam, c->n_int, n_orb, nullptr, 0, nullptr, 0, 0, nullptr, 0, nullptr, 0,
+              accumulate};
+  k_assemble<double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  c->n_launch += 2;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+template <int P1>
+tdks_status cross_t(tdks_ctx* c, const double2* mu, const double2* phi, int n_orb, double coef,
+                    double* gq) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = (((CS + P1) * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
+  TDKS_CU(c, set_smem(k_cross<P1>, smem));
+  k_cross<P1><<<dim3(elem_blocks_t<P1>(c)), dim3(P2, E), smem, c->stream>>>(
+      tdks_geom(c), c->d_tab, mu, phi, c->n_int, n_orb, coef, gq);
+  c->n_launch += 1;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
 
 int hbar_blocks_per_color(const tdks_ctx* c) {
   int b = 0;
@@ -789,13 +988,27 @@ tdks_status launch_stiffness(tdks_ctx* c, const double* in, double* out, double*
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }
 
-tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, double scale) {
-  TDKS_DISPATCH(c->P1, (load_t<P1>(c, f_q, out, scale)));
+tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, double scale,
+                               int weighted) {
+  TDKS_DISPATCH(c->P1, (load_t<P1>(c, f_q, out, scale, weighted)));
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }
 
-tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q) {
-  TDKS_DISPATCH(c->P1, (interp_t<P1>(c, nodal, f_q)));
+tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q, double scale,
+                          int weighted) {
+  TDKS_DISPATCH(c->P1, (interp_t<P1>(c, nodal, f_q, scale, weighted)));
+  return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
+}
+
+tdks_status launch_density_adjoint(tdks_ctx* c, const double2* psi, int n_orb, const double* g_rho,
+                                   double2* lam, int accumulate) {
+  TDKS_DISPATCH(c->P1, (dens_adj_t<P1>(c, psi, n_orb, g_rho, lam, accumulate)));
+  return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
+}
+
+tdks_status launch_cross(tdks_ctx* c, const double2* mu, const double2* phi, int n_orb, double coef,
+                         double* g_q) {
+  TDKS_DISPATCH(c->P1, (cross_t<P1>(c, mu, phi, n_orb, coef, g_q)));
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }
 

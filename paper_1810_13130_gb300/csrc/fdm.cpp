@@ -126,3 +126,9 @@ void tdks_fdm_axis(const Tables1D& t, int p, const double* br, int n_el, std::ve
       S[(size_t)i * n + c] = s / L[(size_t)i * n + i];
     }
 }
+
+// Symmetric eigendecomposition of a small dense matrix (C is overwritten):
+// columns of V are the eigenvectors, lam the eigenvalues.
+void tdks_sym_eigen(std::vector<double>& C, int n, std::vector<double>& V, std::vector<double>& lam) {
+  jacobi_eigen(C, n, V, lam);
+}

@@ -80,6 +80,52 @@ __device__ __forceinline__ double pz81_vxc(double rho) {
   return vx + vc;
 }
 
+// d v_xc / d rho of the same fit (for the adjoint): with x = rho^(1/3) terms
+//   dv_x/drho = -(1/3)(3/pi)^(1/3) rho^(-2/3),  dv_c/drho = dv_c/dr_s * (-r_s / (3 rho))
+//   r_s >= 1: v_c = g N / D^2, dv_c/dr_s = g (N' D - 2 N D') / D^3,
+//             D = 1 + b1 sqrt(rs) + b2 rs, N = 1 + 7/6 b1 sqrt(rs) + 4/3 b2 rs
+//   r_s <  1: dv_c/dr_s = A / rs + 2/3 C (ln rs + 1) + (2D - C)/3
+__device__ __forceinline__ double pz81_fxc(double rho) {
+  if (!(rho >= 1e-14)) return 0.0;
+  const double rs = cbrt(3.0 / (4.0 * M_PI * rho));
+  const double dvx = -(1.0 / 3.0) * cbrt(3.0 / M_PI) / cbrt(rho * rho);
+  double dvc;
+  if (rs >= 1.0) {
+    const double sq = sqrt(rs);
+    const double D = 1.0 + 1.0529 * sq + 0.3334 * rs;
+    const double N = 1.0 + (7.0 / 6.0) * 1.0529 * sq + (4.0 / 3.0) * 0.3334 * rs;
+    const double dD = 0.5 * 1.0529 / sq + 0.3334;
+    const double dN = (7.0 / 12.0) * 1.0529 / sq + (4.0 / 3.0) * 0.3334;
+    dvc = -0.1423 * (dN * D - 2.0 * N * dD) / (D * D * D);
+  } else {
+    dvc = 0.0311 / rs + (2.0 / 3.0) * 0.0020 * (log(rs) + 1.0) + (2.0 * -0.0116 - 0.0020) / 3.0;
+  }
+  return dvx + dvc * (-rs / (3.0 * rho));
+}
+
+__global__ void k_fxc_add(const double* rho, const double* gh, double* grho, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    grho[i] += pz81_fxc(rho[i]) * gh[i];
+}
+
+// g[q] += coef wJ_q (e . x_q): sensitivity of e . mu to rho at the Gauss points
+__global__ void k_dipole_sens(Geom g, const double* eta, const double* w, int P1, long long n,
+                              double coef, double ex, double ey, double ez, double* out) {
+  const int P2 = P1 * P1, P3 = P2 * P1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double x[3];
+    quad_xyz(g, eta, P1, i, x);
+    const long long e = i / P3;
+    const int q = (int)(i - e * P3);
+    const int ix = (int)(e % g.nx), iy = (int)((e / g.nx) % g.ny), iz = (int)(e / ((long long)g.nx * g.ny));
+    const double J = 0.125 * (g.brk[0][ix + 1] - g.brk[0][ix]) * (g.brk[1][iy + 1] - g.brk[1][iy]) *
+                     (g.brk[2][iz + 1] - g.brk[2][iz]);
+    out[i] += coef * J * w[q % P1] * w[(q / P1) % P1] * w[q / P2] * (ex * x[0] + ey * x[1] + ez * x[2]);
+  }
+}
+
 __global__ void k_xc(const double* rho, double* vxc, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -107,7 +153,7 @@ __global__ void k_combine(Geom g, const double* eta, int P1, long long n, double
 
 // Per-block partial sums of J w_qx w_qy w_qz x_q rho_q (3 components).
 __global__ void k_dipole_part(Geom g, const double* eta, const double* w, int P1, long long n,
-                              const double* rho, double* part) {
+                              const double* rho, double* part, int weighted) {
   __shared__ double red[3][kVecThreads / 32];
   double acc[3] = {0.0, 0.0, 0.0};
   const int P2 = P1 * P1, P3 = P2 * P1;
@@ -120,7 +166,7 @@ __global__ void k_dipole_part(Geom g, const double* eta, const double* w, int P1
     const int ex = (int)(e % g.nx), ey = (int)((e / g.nx) % g.ny), ez = (int)(e / ((long long)g.nx * g.ny));
     const double J = 0.125 * (g.brk[0][ex + 1] - g.brk[0][ex]) * (g.brk[1][ey + 1] - g.brk[1][ey]) *
                      (g.brk[2][ez + 1] - g.brk[2][ez]);
-    const double m = J * w[q % P1] * w[(q / P1) % P1] * w[q / P2] * rho[i];
+    const double m = weighted ? J * w[q % P1] * w[(q / P1) % P1] * w[q / P2] * rho[i] : rho[i];
     acc[0] += m * x[0];
     acc[1] += m * x[1];
     acc[2] += m * x[2];
@@ -181,6 +227,24 @@ tdks_status launch_nuclear(tdks_ctx* c) {
   return TDKS_OK;
 }
 
+tdks_status launch_fxc_add(tdks_ctx* c, const double* rho, const double* g_h, double* g_rho) {
+  const long long n = c->n_elem * c->nq3;
+  k_fxc_add<<<vec_grid(n), kVecThreads, 0, c->stream>>>(rho, g_h, g_rho, n);
+  c->n_launch += 1;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+tdks_status launch_dipole_sens(tdks_ctx* c, double coef, const double e[3], double* g_rho) {
+  const long long n = c->n_elem * c->nq3;
+  k_dipole_sens<<<vec_grid(n), kVecThreads, 0, c->stream>>>(
+      tdks_geom(c), c->d_tab + tab_off_eta(c->P1), c->d_tab + tab_off_w(c->P1), c->P1, n, coef,
+      e[0], e[1], e[2], g_rho);
+  c->n_launch += 1;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
 tdks_status launch_xc(tdks_ctx* c, const double* rho, double* vxc) {
   const long long n = c->n_elem * c->nq3;
   k_xc<<<vec_grid(n), kVecThreads, 0, c->stream>>>(rho, vxc, n);
@@ -203,13 +267,14 @@ tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double 
   return TDKS_OK;
 }
 
-tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3]) {
+tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3], int weighted) {
   const long long n = c->n_elem * c->nq3;
   const int nb = vec_grid(n);
   double* part = c->d_part;                 // 3 * nb doubles
   double* out = c->d_part + 3 * kVecBlocks;
   k_dipole_part<<<nb, kVecThreads, 0, c->stream>>>(tdks_geom(c), c->d_tab + tab_off_eta(c->P1),
-                                                   c->d_tab + tab_off_w(c->P1), c->P1, n, rho, part);
+                                                   c->d_tab + tab_off_w(c->P1), c->P1, n, rho, part,
+                                                   weighted);
   k_sum_parts3<<<1, 32, 0, c->stream>>>(part, nb, out);
   c->n_launch += 2;
   TDKS_CU(c, cudaGetLastError());

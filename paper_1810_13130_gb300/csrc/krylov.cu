@@ -380,17 +380,23 @@ tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb) {
   return TDKS_OK;
 }
 
-static tdks_status ensure_krylov(tdks_ctx* c, int n_orb, int kmax) {
-  if (c->d_V && c->V_orb >= n_orb && c->V_kmax == kmax) return TDKS_OK;
-  if (c->d_V) cudaFree(c->d_V);
-  c->d_V = nullptr;
+static tdks_status ensure_krylov(tdks_ctx* c, int w, int n_orb, int kmax) {
+  if (!c->d_kryw[w]) {
+    if (cudaMalloc(&c->d_kryw[w], (size_t)c->n_orb * sizeof(KryOrb)) != cudaSuccess) {
+      cudaGetLastError();
+      return tdks_fail(c, TDKS_ERR_NOMEM, "Lanczos state");
+    }
+  }
+  if (c->d_Vw[w] && c->Vw_orb[w] >= n_orb && c->Vw_kmax[w] == kmax) return TDKS_OK;
+  if (c->d_Vw[w]) cudaFree(c->d_Vw[w]);
+  c->d_Vw[w] = nullptr;
   const size_t bytes = (size_t)n_orb * kmax * c->n_int * sizeof(double2);
-  if (cudaMalloc(&c->d_V, bytes) != cudaSuccess) {
+  if (cudaMalloc(&c->d_Vw[w], bytes) != cudaSuccess) {
     cudaGetLastError();
     return tdks_fail(c, TDKS_ERR_NOMEM, "Krylov basis (" + std::to_string(bytes >> 20) + " MiB)");
   }
-  c->V_orb = n_orb;
-  c->V_kmax = kmax;
+  c->Vw_orb[w] = n_orb;
+  c->Vw_kmax[w] = kmax;
   return TDKS_OK;
 }
 
@@ -398,8 +404,8 @@ struct KrySummary {
   int k, status, k_total, nsub, applies, kseen;
 };
 
-static tdks_status read_summary(tdks_ctx* c, int n_orb, KrySummary* h) {
-  TDKS_CU(c, cudaMemcpy2DAsync(h, sizeof(KrySummary), &c->d_kry[0].k, sizeof(KryOrb),
+static tdks_status read_summary(tdks_ctx* c, const KryOrb* kry, int n_orb, KrySummary* h) {
+  TDKS_CU(c, cudaMemcpy2DAsync(h, sizeof(KrySummary), &kry[0].k, sizeof(KryOrb),
                                sizeof(KrySummary), n_orb, cudaMemcpyDeviceToHost, c->stream));
   TDKS_CU(c, cudaStreamSynchronize(c->stream));
   return TDKS_OK;
@@ -408,12 +414,24 @@ static tdks_status read_summary(tdks_ctx* c, int n_orb, KrySummary* h) {
 tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, double tau,
                      double tol, int kmax, int prec, int* k_used, int* kmax_seen,
                      int64_t* applies, int* nsub) {
+  return run_expm_ws(c, 0, in, out, n_orb, tau, tol, kmax, prec, k_used, kmax_seen, applies, nsub);
+}
+
+// Lanczos exponential with workspace w (0 for propagation; 1 is a second basis
+// kept alive alongside the first by the adjoint).  The basis V_0 = in (when no
+// sub-step is needed), V_1.. in the workspace, and the per-orbital state stay
+// valid until the next call on the same workspace.
+tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int n_orb, double tau,
+                        double tol, int kmax, int prec, int* k_used, int* kmax_seen,
+                        int64_t* applies, int* nsub) {
   if (kmax < 1 || kmax > TDKS_KMAX) return tdks_fail(c, TDKS_ERR_ARG, "k_max must be in [1, 128]");
   if (n_orb < 1 || n_orb > c->n_orb) return tdks_fail(c, TDKS_ERR_ARG, "n_orb out of range");
   const long long n = c->n_int;
   const int bpc = hbar_blocks_per_color(c);
   TDKS_TRY(ensure_part(c, n_orb, 8 * (int64_t)bpc));
-  TDKS_TRY(ensure_krylov(c, n_orb, kmax));
+  TDKS_TRY(ensure_krylov(c, w, n_orb, kmax));
+  KryOrb* kry = c->d_kryw[w];
+  double2* VW = c->d_Vw[w];
   const int64_t ps = c->part_stride;
   double* apart = c->d_part;
   double* npart = c->d_part + (int64_t)c->n_orb * ps;
@@ -421,7 +439,7 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
   const int nasm = assemble_blocks(c, n_orb);   // partials of ||w||^2 per orbital
   const int64_t wsorb = (int64_t)kmax * n;   // stride between orbitals in the workspace
   std::vector<KrySummary> h(n_orb);
-  k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb, tau);
+  k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(kry, n_orb, tau);
   c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   if (c->timing && !c->ev[0]) {
@@ -431,26 +449,26 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
   int n_active = n_orb;
   const double2* cur = in;
   for (int sub = 0; sub <= TDKS_MAX_SUBSTEPS; ++sub) {
-    k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(cur, n, n, c->d_kry, npart, ps);
-    k_kry_start<<<n_orb, kThreads, 0, c->stream>>>(c->d_kry, npart, ps, nb);
+    k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(cur, n, n, kry, npart, ps);
+    k_kry_start<<<n_orb, kThreads, 0, c->stream>>>(kry, npart, ps, nb);
     c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
     for (int j = 0; j < kmax; ++j) {
-      const double2* Vj = (j == 0) ? cur : c->d_V + (int64_t)(j - 1) * n;
+      const double2* Vj = (j == 0) ? cur : VW + (int64_t)(j - 1) * n;
       const int64_t sj = (j == 0) ? n : wsorb;
-      const double2* Vm = (j == 1) ? cur : (j >= 2 ? c->d_V + (int64_t)(j - 2) * n : nullptr);
+      const double2* Vm = (j == 1) ? cur : (j >= 2 ? VW + (int64_t)(j - 2) * n : nullptr);
       const int64_t sm = (j == 1) ? n : wsorb;
-      double2* Vn = c->d_V + (int64_t)j * n;
+      double2* Vn = VW + (int64_t)j * n;
       // Hbar q_j and the three-term update fused: V_{j+1} = Hbar q_j - alpha_j q_j - beta q_{j-1}
-      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, c->d_kry, j, apart, ps, 1, Vm, sm, npart, ps};
+      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, kry, j, apart, ps, 1, Vm, sm, npart, ps, 0};
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[0], c->stream));
       TDKS_TRY(launch_hbar_apply(c, a, prec));
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
       c->n_apply_units += (int64_t)n_active * c->n_elem;
-      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, c->d_kry, npart, ps, nasm);
+      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm);
       c->n_launch += 1;
       TDKS_CU(c, cudaGetLastError());
-      TDKS_TRY(read_summary(c, n_orb, h.data()));
+      TDKS_TRY(read_summary(c, kry, n_orb, h.data()));
       if (c->timing) {
         float ms = 0.f;
         TDKS_CU(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
@@ -460,12 +478,12 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
       for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
       if (!n_active) break;
     }
-    k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, c->d_V, wsorb,
-                                                             kmax, c->d_kry);
-    k_kry_after<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(c->d_kry, n_orb);
+    k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb,
+                                                             kmax, kry);
+    k_kry_after<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(kry, n_orb);
     c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
-    TDKS_TRY(read_summary(c, n_orb, h.data()));
+    TDKS_TRY(read_summary(c, kry, n_orb, h.data()));
     bool any = false, failed = false;
     for (int o = 0; o < n_orb; ++o) {
       any |= (h[o].status == KRY_ACTIVE);

@@ -417,7 +417,8 @@ tdks_status poisson_setup(tdks_ctx* c, const Tables1D& t) {
   return TDKS_OK;
 }
 
-tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters) {
+// Solve K x = b by the preconditioned CG above; x holds the initial guess.
+tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters) {
   const long long n = c->n_int;
   const int nb = grid_for(n);
   const int sbpc = stiff_blocks_per_color(c);
@@ -425,13 +426,10 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
   double* part_pAp = c->d_part;                       // 8 * sbpc
   double* part_vec = c->d_part + 8 * (int64_t)sbpc;   // 2 * nb
   CgState* cg = c->d_cg;
-  // b = 4 pi c
-  TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
-  TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
   // r = b - K x0
   TDKS_CU(c, cudaMemsetAsync(c->d_Ap, 0, n * sizeof(double), c->stream));
-  TDKS_TRY(launch_stiffness(c, c->d_phi, c->d_Ap, nullptr, nullptr));
-  k_cg_init<<<nb, kThreads, 0, c->stream>>>(n, c->d_b, c->d_Ap, c->d_r, part_vec);
+  TDKS_TRY(launch_stiffness(c, x, c->d_Ap, nullptr, nullptr));
+  k_cg_init<<<nb, kThreads, 0, c->stream>>>(n, b, c->d_Ap, c->d_r, part_vec);
   k_cg_init_fin<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, cg);
   c->n_launch += 2;
   // z = P^-1 r; rz = r.z; p = z (first direction) or z + beta p
@@ -456,7 +454,7 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
     while (it < next_poll) {
       TDKS_CU(c, cudaMemsetAsync(c->d_Ap, 0, n * sizeof(double), c->stream));
       TDKS_TRY(launch_stiffness(c, c->d_pv, c->d_Ap, part_pAp, cg));
-      k_cg_update<<<nb, kThreads, 0, c->stream>>>(n, part_pAp, 8 * sbpc, c->d_phi, c->d_r, c->d_pv,
+      k_cg_update<<<nb, kThreads, 0, c->stream>>>(n, part_pAp, 8 * sbpc, x, c->d_r, c->d_pv,
                                                   c->d_Ap, part_vec, cg);
       k_cg_fin_rr<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, c->cg_maxit, cg);
       c->n_launch += 2;
@@ -473,12 +471,21 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
   if (iters) *iters = host.iters;
   c->n_cg += host.iters;
   if (host.failed == 3) {
-    TDKS_CU(c, cudaMemsetAsync(c->d_phi, 0, n * sizeof(double), c->stream));
+    TDKS_CU(c, cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
     host.failed = 0;
   }
   if (host.failed == 1) return tdks_fail(c, TDKS_ERR_NAN, "non-finite residual in Poisson CG");
   if (host.failed == 2 || !host.done)
     return tdks_fail(c, TDKS_ERR_NOT_CONVERGED, "Poisson CG reached its iteration cap");
+  return TDKS_OK;
+}
+
+tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters) {
+  const long long n = c->n_int;
+  // b = 4 pi c
+  TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
+  TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
+  TDKS_TRY(run_cg_solve(c, c->d_b, c->d_phi, iters));
   TDKS_TRY(launch_interp(c, c->d_phi, vh_q));
   return TDKS_OK;
 }

@@ -95,10 +95,9 @@ struct tdks_ctx {
   double* d_fdmL[3] = {nullptr, nullptr, nullptr};    // per-axis eigenvalues
   double *d_z = nullptr, *d_t1 = nullptr, *d_t2 = nullptr, *d_invdiag = nullptr;
   // Krylov
-  double2* d_V = nullptr;      // [n_orb][kmax][n_int]
-  int V_orb = 0, V_kmax = 0;
-  KryOrb* d_kry = nullptr;
-  KryOrb* h_kry = nullptr;     // pinned mirror (status reads)
+  double2* d_Vw[2] = {nullptr, nullptr};      // Krylov bases [n_orb][kmax][n_int]
+  int Vw_orb[2] = {0, 0}, Vw_kmax[2] = {0, 0};
+  KryOrb* d_kryw[2] = {nullptr, nullptr};     // per-orbital Lanczos state of each basis
   double2* d_psi_half = nullptr;
   void* d_evec = nullptr;      // element-local Hbar results [n_orb][n_elem][P1^3] (complex)
   size_t evec_bytes = 0;
@@ -109,6 +108,7 @@ struct tdks_ctx {
   double* h_red = nullptr;     // pinned small host buffer
   int* h_int = nullptr;
   bool propagation_ready = false;
+  void* adj = nullptr;          // objective / adjoint state (adjoint.cu)
   // counters
   int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0;
   double apply_ms = 0.0;
@@ -190,21 +190,40 @@ struct ApplyArgs {
   int64_t vm_stride;
   double* npart;              // per-block partials of ||out||^2 per orbital
   int64_t npart_stride;
+  int accumulate;             // out += result instead of out = result (plain apply only)
 };
 tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec);
 tdks_status launch_stiffness(tdks_ctx* c, const double* in, double* out, double* part,
                              const CgState* cg);
-tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, double scale);
-tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q);
+tdks_status launch_load_vector(tdks_ctx* c, const double* f_q, double* out, double scale,
+                               int weighted = 1);
+tdks_status launch_interp(tdks_ctx* c, const double* nodal, double* f_q, double scale = 1.0,
+                          int weighted = 0);
+// adjoint kernels (elements.cu)
+// lam_a (+)= 2 occ_a M^-1/2 (B^T)^(x)3 (g_rho psi_a(x_q))
+tdks_status launch_density_adjoint(tdks_ctx* c, const double2* psi, int n_orb, const double* g_rho,
+                                   double2* lam, int accumulate);
+// g_q += coef wJ_q sum_a Im(conj(mu_a(x_q)) phi_a(x_q))
+tdks_status launch_cross(tdks_ctx* c, const double2* mu, const double2* phi, int n_orb, double coef,
+                         double* g_q);
 tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q);
 int hbar_blocks_per_color(const tdks_ctx* c);
 int assemble_blocks(const tdks_ctx* c, int n_orb);   // partial-sum count of the fused update
 int stiff_blocks_per_color(const tdks_ctx* c);
 
+// magnus step with optional recording of the intermediates (capi.cu)
+tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, const double Eq[3],
+                             const double Eh[3], double tol, int k_max, int prec, tdks_stats* st,
+                             double2* keep_half, double* keep_vpred, double* keep_vmid);
+void adjoint_free(tdks_ctx* c);
+void tdks_sym_eigen(std::vector<double>& C, int n, std::vector<double>& V, std::vector<double>& lam);
+
 // fields.cu
+tdks_status launch_fxc_add(tdks_ctx* c, const double* rho, const double* g_h, double* g_rho);
+tdks_status launch_dipole_sens(tdks_ctx* c, double coef, const double e[3], double* g_rho);
 tdks_status launch_nuclear(tdks_ctx* c);
 tdks_status launch_xc(tdks_ctx* c, const double* rho, double* vxc);
-tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3]);
+tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3], int weighted = 1);
 tdks_status launch_kick(tdks_ctx* c, double2* psi, int n_orb, double kappa, const double dir[3]);
 // v_out = vn + a1*h1 + a2*h2 + h3 - E.x_q   (h2/h3 may be null)
 tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double a1,
@@ -213,12 +232,16 @@ tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double 
 
 // poisson.cu
 tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters);
+tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters);
 tdks_status poisson_setup(tdks_ctx* c, const Tables1D& t);
 
 // krylov.cu
 tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, double tau,
                      double tol, int kmax, int prec, int* k_used, int* kmax_seen,
                      int64_t* applies, int* nsub);
+tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int n_orb, double tau,
+                        double tol, int kmax, int prec, int* k_used, int* kmax_seen,
+                        int64_t* applies, int* nsub);
 
 // reduction helper used by several files
 tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);

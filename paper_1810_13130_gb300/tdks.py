@@ -88,6 +88,8 @@ def lib():
         "tdks_last_error": [v],
         "tdks_status_string": [i],
         "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
+        "tdks_objective_forward": [v, p, i, i, d, _dp, _dp, _dp, i, d, i, i, _dp, _dp],
+        "tdks_objective_backward": [v, i, _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -103,7 +105,8 @@ def exported_symbols() -> list:
                         "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
-                        "tdks_dipole_noalloc", "tdks_last_error", "tdks_status_string")]
+                        "tdks_dipole_noalloc", "tdks_objective_forward",
+                        "tdks_objective_backward", "tdks_last_error", "tdks_status_string")]
 
 
 def _darr(a) -> np.ndarray:
@@ -309,3 +312,58 @@ class Context:
             None if Eh is None else Eh.ctypes.data, tol, k_max, prec, dip.ctypes.data),
             "tdks_propagate_host")
         return dip[:n_steps]
+
+    def objective_forward(self, psi0: torch.Tensor, E: np.ndarray, w, e, dt: float,
+                          ckpt_every: int = 10, tol: float = 1e-10, k_max: int = 64,
+                          prec: int = FP64):
+        """J = sum_n w_n (e . mu_n)^2 over the propagation from psi0 with field samples
+        E ([n_steps, 6]); returns (J, dipoles [n_steps + 1, 3]).  Keeps checkpoints
+        for objective_backward."""
+        Eh = _darr(E).reshape(-1, 6)
+        n = Eh.shape[0]
+        wh = _darr(w).reshape(-1)
+        if wh.shape[0] != n + 1:
+            raise TDKSError("objective_forward: w needs n_steps + 1 weights")
+        eh = _darr(e).reshape(3)
+        J = C.c_double(0.0)
+        dip = np.zeros((n + 1, 3))
+        self._sync_stream()
+        self._check(lib().tdks_objective_forward(
+            self.h, _dev(psi0, torch.complex128, "psi0"), psi0.shape[0], n, dt, _ptr(Eh), _ptr(wh),
+            _ptr(eh), ckpt_every, tol, k_max, prec, C.byref(J), _ptr(dip)), "tdks_objective_forward")
+        self._n_obj_steps = n
+        return J.value, dip
+
+    def objective_backward(self, n_s: int = 8) -> np.ndarray:
+        """dJ/dE ([n_steps, 6]) of the last objective_forward call."""
+        n = getattr(self, "_n_obj_steps", 0)
+        g = np.zeros((max(n, 1), 6))
+        self._sync_stream()
+        self._check(lib().tdks_objective_backward(self.h, n_s, _ptr(g)), "tdks_objective_backward")
+        return g[:n]
+
+
+class DipoleObjective(torch.autograd.Function):
+    """J(E) = sum_n w_n (e . mu_n)^2 as a differentiable function of the field samples
+    E ([n_steps, 6], float64, any device): forward propagates on the GPU with
+    checkpoints, backward runs the adjoint sweep (no autograd tape of the propagation).
+
+        J = DipoleObjective.apply(E, ctx, psi0, w, e, dt, ckpt_every, tol, k_max, prec, n_s)
+    """
+
+    @staticmethod
+    def forward(fctx, E, tdctx, psi0, w, e, dt, ckpt_every=10, tol=1e-10, k_max=64, prec=FP64,
+                n_s=8):
+        J, _ = tdctx.objective_forward(psi0, E.detach().cpu().numpy(), w, e, dt, ckpt_every, tol,
+                                       k_max, prec)
+        fctx.tdctx = tdctx
+        fctx.n_s = n_s
+        fctx.E_meta = (E.device, E.dtype, E.shape)
+        return torch.tensor(J, dtype=E.dtype, device=E.device)
+
+    @staticmethod
+    def backward(fctx, gJ):
+        dev, dt_, shape = fctx.E_meta
+        g = fctx.tdctx.objective_backward(fctx.n_s)
+        gE = torch.from_numpy(g).to(device=dev, dtype=dt_).reshape(shape) * gJ
+        return (gE,) + (None,) * 10

@@ -139,6 +139,79 @@ def config3() -> SystemConfig:
         dt=0.01, n_steps=1000, tol=1e-10, k_max=64)
 
 
+@dataclasses.dataclass
+class PulseConfig:
+    """A train of Gaussian-envelope laser pulses along `direction`:
+    E(t) = sum_j a_j exp(-(t - t_j)^2 / (2 sigma^2)) sin(omega t + phi_j)."""
+    omega: float
+    sigma: float
+    centers: np.ndarray
+    a: np.ndarray
+    phi: np.ndarray
+    direction: tuple
+    n_steps: int
+    dt: float
+    ckpt_every: int
+    fd_h: float
+
+    @property
+    def params(self) -> np.ndarray:
+        """The 2 n_pulses parameters (a_1.., phi_1..)."""
+        return np.concatenate([self.a, self.phi])
+
+    def objective_weights(self) -> np.ndarray:
+        """Trapezoid weights of int d(t)^2 dt over the n_steps + 1 dipole samples."""
+        w = np.full(self.n_steps + 1, self.dt)
+        w[0] = w[-1] = 0.5 * self.dt
+        return w
+
+
+PULSE_SEED = 18101304
+
+
+def config4():
+    """The atom of config1 driven by four seeded Gaussian pulses (no kick), 200 steps."""
+    sc = config1()
+    sc.name = "atom_soft_Z2_6x6x6_p4_pulses"
+    sc.kick = 0.0
+    sc.dt = 0.1
+    sc.n_steps = 200
+    rng = np.random.default_rng(PULSE_SEED)
+    pc = PulseConfig(omega=0.3, sigma=5.0, centers=np.array([4.0, 8.0, 12.0, 16.0]),
+                     a=rng.uniform(0.5e-3, 1.5e-3, size=4), phi=rng.uniform(0.0, 2 * math.pi, size=4),
+                     direction=(0.0, 0.0, 1.0), n_steps=200, dt=0.1, ckpt_every=20, fd_h=1e-5)
+    return sc, pc
+
+
+def pulse_samples(params, pc: PulseConfig):
+    """Field samples of the predictor-corrector steps, [n_steps, 6]: E at t_n + dt/4
+    then at t_n + dt/2 (t_n = n dt).  params = (a_1.., phi_1..) as a numpy array or a
+    float64 torch tensor (differentiable)."""
+    n_p = len(pc.centers)
+    t = np.arange(pc.n_steps) * pc.dt
+    tt = np.stack([t + 0.25 * pc.dt, t + 0.5 * pc.dt], axis=1)          # [n, 2]
+    d = np.asarray(pc.direction, float)
+    try:
+        import torch
+        is_t = isinstance(params, torch.Tensor)
+    except ImportError:
+        is_t = False
+    if is_t:
+        a, ph = params[:n_p], params[n_p:]
+        T = torch.as_tensor(tt, dtype=params.dtype, device=params.device)[..., None]
+        c = torch.as_tensor(pc.centers, dtype=params.dtype, device=params.device)
+        env = torch.exp(-(T - c) ** 2 / (2 * pc.sigma ** 2))
+        e = (a * env * torch.sin(pc.omega * T + ph)).sum(-1)            # [n, 2]
+        D = torch.as_tensor(d, dtype=params.dtype, device=params.device)
+        return (e[..., None] * D).reshape(pc.n_steps, 6)
+    params = np.asarray(params, float)
+    a, ph = params[:n_p], params[n_p:]
+    T = tt[..., None]
+    env = np.exp(-(T - pc.centers) ** 2 / (2 * pc.sigma ** 2))
+    e = (a * env * np.sin(pc.omega * T + ph)).sum(-1)
+    return (e[..., None] * d).reshape(pc.n_steps, 6)
+
+
 def small_config(nx=3, ny=2, nz=2, p=3, n_orb=2, L=6.0, seed=7, nuc_kind="soft",
                  hartree=True, xc=True, graded=False) -> SystemConfig:
     """A small test system with uneven element counts and (optionally) uneven sizes."""
