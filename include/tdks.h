@@ -232,6 +232,59 @@ tdks_status tdks_objective_forward(tdks_ctx* ctx, const double* psi0, int n_orb,
                                    int prec, double* J_host, double* dip_host);
 tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
 
+/* Batched propagation of many independent systems (no counterpart in the paper,
+ * which propagates one system at a time: a throughput form of the same step).
+ *
+ * Each system has its own mesh, degree, orbitals, nuclei and time step; all
+ * advance together by the predictor-corrector Magnus step of Sec. VI.B with no
+ * external field.  One step of all systems is one CUDA graph replay; the Krylov
+ * loops run on the device (conditional graph nodes) and the Poisson CG of every
+ * system takes a fixed number of fast-diagonalization-preconditioned iterations
+ * (each system's axes must have <= 1024 interior nodes, else TDKS_ERR_ARG).
+ *
+ * tdks_batch_create: n_sys systems; meshes/systems as for tdks_create, dt[n_sys]
+ *   (> 0), contraction precision prec (TDKS_FP64/FP32/DF64), Lanczos tolerance
+ *   and k_max (2..128).  The batch owns one CUDA stream (tdks_batch_stream) on
+ *   which all its work runs, the orbitals of every system and all workspaces
+ *   (Krylov basis: n_orb x k_max x n_int complex per system).
+ * tdks_batch_set_orbitals / get_orbitals: device copies of one system's block
+ *   [n_orb][n_int] complex128 (tdks_batch_sizes gives the sizes).
+ * tdks_batch_kick: psi_s <- exp(-i kappa[s] r . dir[s]) psi_s (Sec. VII.A).
+ * tdks_batch_init: V_HXC history and the dipoles ([n_sys][3]) of the current
+ *   orbitals (as tdks_init_propagation for every system).
+ * tdks_batch_tune: chooses the elements per CTA of every degree and the orbitals
+ *   per work item of every (degree, orbital count) class by timing `reps`
+ *   launches of each candidate; writes up to cap choices (tile table) to out.
+ *   Optional; without it the largest tile and one orbital per item are used.
+ * tdks_batch_steps: n_steps steps of every system; dipoles [n_steps][n_sys][3].
+ *   Synchronizes.  TDKS_ERR_NOT_CONVERGED if a Lanczos loop failed or hit its
+ *   pass cap (16 k_max passes) or a Poisson solve did not converge.
+ * tdks_batch_stats: sum over orbital-vector Hbar applications of the system's
+ *   interior DoF count, and the largest Krylov dimension seen. */
+typedef struct tdks_batch tdks_batch;
+typedef struct {
+  int p;                /* degree of the class                                  */
+  int n_orb;            /* orbital count of the class                           */
+  int elems_per_cta;    /* tile: elements per CTA chosen for the degree          */
+  int orbs_per_item;    /* tile: orbitals per work item chosen for the class     */
+  double ms;            /* measured apply time of the class with that tile       */
+} tdks_tile_choice;
+tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes,
+                              const tdks_system_desc* systems, const double* dt, int prec,
+                              double tol, int k_max, tdks_batch** out);
+tdks_status tdks_batch_destroy(tdks_batch* b);
+void* tdks_batch_stream(tdks_batch* b);
+tdks_status tdks_batch_sizes(const tdks_batch* b, int sys, int64_t* n_int, int64_t* n_elem,
+                             int* nq3, int* n_orb);
+tdks_status tdks_batch_set_orbitals(tdks_batch* b, int sys, const double* psi_dev);
+tdks_status tdks_batch_get_orbitals(tdks_batch* b, int sys, double* psi_dev);
+tdks_status tdks_batch_kick(tdks_batch* b, const double* kappa, const double* dir);
+tdks_status tdks_batch_init(tdks_batch* b, double* dip_host);
+tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out);
+tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host);
+tdks_status tdks_batch_stats(tdks_batch* b, int64_t* dof_applies, int* k_max_seen, int reset);
+const char* tdks_batch_last_error(const tdks_batch* b);
+
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar
  * colour launches, element-orbital applications, and -- when timing is on --
  * the summed device time of the Hbar applications inside tdks_expm measured

@@ -1,0 +1,648 @@
+// Batched propagation of many independent systems (uneven meshes, degrees and
+// orbital counts) by the same launches.
+//
+// One Magnus predictor-corrector step (Sec. VI.B, Eqs. 25-26) of every system is
+// one CUDA graph:
+//   V_pred of every system                       (per-system kernels)
+//   WHILE (some orbital active): one pass of the batched Lanczos exponential
+//     exp(-i dt/2 Hbar) psi -> psi_half           (conditional graph node)
+//   density, Hartree (fixed-length CG), LDA, V_mid of every system
+//   WHILE: exp(-i dt Hbar) psi -> psi               (conditional graph node)
+//   V_HXC history, dipole of every system
+// A pass of the loop body is a handful of launches covering all systems: the
+// apply is a persistent kernel per degree class walking a work list of
+// (system, element block, orbital block) tiles; norms, assembly with the fused
+// three-term update, the small exponentials and the recombination are one launch
+// each over all (system, orbital) pairs.  Every orbital carries its own Lanczos
+// state, so systems with different Krylov dimensions, time steps and sub-steps
+// progress independently; the loop ends on the device when all are done (or at
+// a pass cap, reported as an error).  The host reads nothing inside a step.
+//
+// Tiles: the elements per CTA (E) of each degree and the orbitals per work item
+// of each (degree, orbital count) class are chosen by timing the candidates on
+// the batch itself (tdks_batch_tune).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "tdks_internal.h"
+
+namespace {
+
+constexpr int kMaxSubPasses = 16;
+std::string g_create_err;           // message of the last failed tdks_batch_create   // loop cap = kMaxSubPasses * k_max passes
+
+struct Deg {
+  int P1 = 0, E = 1, grid = 1, n_items = 0;
+  BItem* d_items = nullptr;
+  const void* tab = nullptr;
+};
+
+}  // namespace
+
+struct tdks_batch {
+  int n_sys = 0, prec = 0, kmax = 64, cg_iters = 4, n_sm = 152;
+  double tol = 1e-10;
+  cudaStream_t st = nullptr, st_body = nullptr;
+  std::vector<tdks_ctx*> ctx;
+  std::vector<int> n_orb, n_eblk, n_rblk, opb;
+  std::vector<double> dt;
+  std::vector<double2*> psi, psi_half, Vw;
+  std::vector<KryOrb*> kry;
+  std::vector<void*> ev;
+  std::vector<double*> apart, npart;
+  std::vector<BSys> h_half, h_full;
+  BSys *d_half = nullptr, *d_full = nullptr;
+  BOrb* d_orbs = nullptr;
+  int n_gorb = 0;
+  BRow *d_rows = nullptr, *d_rows_asm = nullptr;
+  int n_rows = 0;
+  std::vector<Deg> degs;
+  int* d_ctrl = nullptr;            // [0], [1]: pass counters, [2]: error bits, [3]: step, [4]: k seen
+  unsigned long long* d_dof = nullptr;
+  double* d_dip = nullptr;
+  int dip_cap = 256;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool orbitals_set = false, ready = false;
+  std::vector<tdks_tile_choice> tiles;
+  std::string err;
+};
+
+namespace {
+
+tdks_status bfail(tdks_batch* b, tdks_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+#define B_CU(b, call)                                                             \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      cudaGetLastError();                                                         \
+      return bfail(b, TDKS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                             \
+  } while (0)
+
+#define B_TRY(b, call, who)                                                       \
+  do {                                                                            \
+    tdks_status s_ = (call);                                                      \
+    if (s_ != TDKS_OK) return bfail(b, s_, std::string(who) + ": " + (b)->err);   \
+  } while (0)
+
+template <typename T>
+tdks_status balloc(tdks_batch* b, T** p, size_t count) {
+  if (cudaMalloc((void**)p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, TDKS_ERR_NOMEM, "batch buffers");
+  }
+  return TDKS_OK;
+}
+
+tdks_status ctx_try(tdks_batch* b, tdks_ctx* c, tdks_status s) {
+  if (s != TDKS_OK) b->err = c ? c->err : std::string("context");
+  return s;
+}
+
+void free_batch(tdks_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto* p : b->psi) cudaFree(p);
+  for (auto* p : b->psi_half) cudaFree(p);
+  for (auto* p : b->Vw) cudaFree(p);
+  for (auto* p : b->kry) cudaFree(p);
+  for (auto* p : b->ev) cudaFree(p);
+  for (auto* p : b->apart) cudaFree(p);
+  for (auto* p : b->npart) cudaFree(p);
+  for (auto& d : b->degs) cudaFree(d.d_items);
+  void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_dof, b->d_dip};
+  for (void* p : ptrs) cudaFree(p);
+  for (auto* c : b->ctx) tdks_destroy(c);
+  if (b->st_body) cudaStreamDestroy(b->st_body);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+void invalidate_graph(tdks_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+int emax_of(int P1) { return std::max(1, 256 / (P1 * P1)); }
+
+// Work list of one degree class with E elements per tile and opb[s] orbitals per item,
+// larger items first (static striding of the persistent grid then balances better).
+std::vector<BItem> make_items(const tdks_batch* b, int P1, int E, const std::vector<int>& opb,
+                              const std::vector<int>* only) {
+  std::vector<BItem> items;
+  for (int s = 0; s < b->n_sys; ++s) {
+    if (b->ctx[s]->P1 != P1) continue;
+    if (only && std::find(only->begin(), only->end(), s) == only->end()) continue;
+    const long long ne = b->ctx[s]->n_elem;
+    const int nb = (int)((ne + E - 1) / E);
+    const int ob = std::max(1, opb[s]);
+    for (int eb = 0; eb < nb; ++eb)
+      for (int o0 = 0; o0 < b->n_orb[s]; o0 += ob)
+        items.push_back(BItem{s, eb, o0, std::min(o0 + ob, b->n_orb[s])});
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const BItem& x, const BItem& y) { return (x.o1 - x.o0) > (y.o1 - y.o0); });
+  return items;
+}
+
+tdks_status upload_descriptors(tdks_batch* b) {
+  for (int s = 0; s < b->n_sys; ++s) {
+    b->h_half[s].n_eblk = b->n_eblk[s];
+    b->h_full[s].n_eblk = b->n_eblk[s];
+  }
+  B_CU(b, cudaMemcpyAsync(b->d_half, b->h_half.data(), b->n_sys * sizeof(BSys), cudaMemcpyHostToDevice, b->st));
+  B_CU(b, cudaMemcpyAsync(b->d_full, b->h_full.data(), b->n_sys * sizeof(BSys), cudaMemcpyHostToDevice, b->st));
+  B_CU(b, cudaStreamSynchronize(b->st));
+  return TDKS_OK;
+}
+
+// (Re)build the work list of degree class d with elements-per-tile E and the
+// current per-system orbital blocks.
+tdks_status build_degree(tdks_batch* b, Deg& d, int E) {
+  d.E = E;
+  for (int s = 0; s < b->n_sys; ++s)
+    if (b->ctx[s]->P1 == d.P1) b->n_eblk[s] = (int)((b->ctx[s]->n_elem + E - 1) / E);
+  std::vector<BItem> items = make_items(b, d.P1, E, b->opb, nullptr);
+  cudaFree(d.d_items);
+  d.d_items = nullptr;
+  B_TRY(b, balloc(b, &d.d_items, items.size()), "work list");
+  B_CU(b, cudaMemcpy(d.d_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice));
+  d.n_items = (int)items.size();
+  int occ = 0;
+  const cudaError_t ce = hbar_batch_occupancy(d.P1, b->prec, E, &occ);
+  if (ce != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return bfail(b, TDKS_ERR_CUDA, "occupancy query of the batched apply (p = " + std::to_string(d.P1 - 1) +
+                                       ", E = " + std::to_string(E) + "): " + cudaGetErrorString(ce) +
+                                       ", blocks/SM " + std::to_string(occ));
+  }
+  d.grid = std::max(1, std::min(d.n_items, occ * b->n_sm));
+  return TDKS_OK;
+}
+
+// Capture of one pass of the batched exponential loop body (on the body stream).
+tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphConditionalHandle h) {
+  cudaStream_t s = b->st_body;
+  B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
+  for (const Deg& d : b->degs)
+    B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, s));
+  B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
+  B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
+  B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, s));
+  B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
+  B_CU(b, launch_bloop_control(h, sys, b->d_orbs, b->n_gorb, iter, kMaxSubPasses * b->kmax,
+                               b->d_ctrl + 2, s));
+  return TDKS_OK;
+}
+
+// Inside an active capture of b->st: append a WHILE node on handle h whose body is
+// one pass of the batched exponential over `sys`.
+tdks_status add_loop(tdks_batch* b, const BSys* sys, int* iter, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  B_CU(b, cudaStreamGetCaptureInfo(b->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return bfail(b, TDKS_ERR_CUDA, "stream is not capturing");
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  B_CU(b, cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  B_CU(b, cudaStreamUpdateCaptureDependencies(b->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  B_CU(b, cudaStreamBeginCaptureToGraph(b->st_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  tdks_status s = capture_body(b, sys, iter, h);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->st_body, &out);
+  if (s != TDKS_OK) return s;
+  if (e != cudaSuccess) return bfail(b, TDKS_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
+  return TDKS_OK;
+}
+
+tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2) {
+  const double zero[3] = {0.0, 0.0, 0.0};
+  int* err = b->d_ctrl + 2;
+  // predictor potential V_N + 1.25 V_HXC^{n-1} - 0.25 V_HXC^{n-2} (no external field)
+  for (int s = 0; s < b->n_sys; ++s) {
+    tdks_ctx* c = b->ctx[s];
+    B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.25, c->d_vhxc1, -0.25, c->d_vhxc2,
+                                          nullptr, zero)), "predictor");
+  }
+  B_CU(b, launch_bkry_init(b->d_half, b->d_orbs, b->n_gorb, 0.5, b->st));
+  B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->st));
+  B_TRY(b, add_loop(b, b->d_half, b->d_ctrl + 0, h1), "half step");
+  B_CU(b, launch_bkry_stats(b->d_half, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  // corrector potential from the density of psi^{n-1/2}
+  for (int s = 0; s < b->n_sys; ++s) {
+    tdks_ctx* c = b->ctx[s];
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err)),
+          "corrector");
+    B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr,
+                                          zero)), "corrector");
+  }
+  B_CU(b, launch_bkry_init(b->d_full, b->d_orbs, b->n_gorb, 1.0, b->st));
+  B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->st));
+  B_TRY(b, add_loop(b, b->d_full, b->d_ctrl + 1, h2), "full step");
+  B_CU(b, launch_bkry_stats(b->d_full, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  // history and dipole of every system
+  for (int s = 0; s < b->n_sys; ++s) {
+    tdks_ctx* c = b->ctx[s];
+    const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
+    B_CU(b, cudaMemcpyAsync(c->d_vhxc2, c->d_vhxc1, fb, cudaMemcpyDeviceToDevice, b->st));
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err)), "history");
+    B_TRY(b, ctx_try(b, c, dipole_graph(c, c->d_rho, b->d_dip + 3 * (size_t)s, b->d_ctrl + 3,
+                                        3 * (int64_t)b->n_sys)), "dipole");
+  }
+  B_CU(b, launch_counter_add(b->d_ctrl + 3, 1, b->st));
+  return TDKS_OK;
+}
+
+tdks_status build_graph(tdks_batch* b) {
+  invalidate_graph(b);
+  B_CU(b, cudaGraphCreate(&b->graph, 0));
+  cudaGraphConditionalHandle h1, h2;
+  // default 0: a loop runs only after its begin kernel set the condition to 1
+  B_CU(b, cudaGraphConditionalHandleCreate(&h1, b->graph, 0, cudaGraphCondAssignDefault));
+  B_CU(b, cudaGraphConditionalHandleCreate(&h2, b->graph, 0, cudaGraphCondAssignDefault));
+  B_CU(b, cudaStreamBeginCaptureToGraph(b->st, b->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  tdks_status s = capture_step(b, h1, h2);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->st, &out);
+  if (s != TDKS_OK) {
+    invalidate_graph(b);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    invalidate_graph(b);
+    return bfail(b, TDKS_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+  }
+  B_CU(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return TDKS_OK;
+}
+
+// time `reps` launches of one degree class's apply with the given work list
+tdks_status time_apply(tdks_batch* b, const Deg& d, const std::vector<BItem>& items, int E, int reps,
+                       double* ms) {
+  BItem* di = nullptr;
+  B_TRY(b, balloc(b, &di, items.size()), "tuning");
+  cudaMemcpy(di, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+  int occ = 0;
+  hbar_batch_occupancy(d.P1, b->prec, E, &occ);
+  const int grid = std::max(1, std::min((int)items.size(), std::max(occ, 1) * b->n_sm));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, b->st);
+  cudaEventRecord(e0, b->st);
+  for (int r = 0; r < reps && ce == cudaSuccess; ++r)
+    ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, b->st);
+  cudaEventRecord(e1, b->st);
+  cudaError_t se = cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(di);
+  if (ce != cudaSuccess || se != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, TDKS_ERR_CUDA, std::string("tuning launch: ") + cudaGetErrorString(ce != cudaSuccess ? ce : se));
+  }
+  *ms = t / std::max(reps, 1);
+  return TDKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdks_system_desc* systems,
+                              const double* dt, int prec, double tol, int k_max, tdks_batch** out) {
+  if (!out) return TDKS_ERR_ARG;
+  *out = nullptr;
+  if (n_sys < 1 || !meshes || !systems || !dt) return TDKS_ERR_ARG;
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64) return TDKS_ERR_ARG;
+  if (k_max < 2 || k_max > TDKS_KMAX || !(tol > 0)) return TDKS_ERR_ARG;
+  tdks_batch* b = new tdks_batch();
+  b->n_sys = n_sys;
+  b->prec = prec;
+  b->tol = tol;
+  b->kmax = k_max;
+  auto fail = [&](tdks_status s) {
+    // the batch is freed: its message moves to the global slot (tdks_batch_last_error(NULL))
+    g_create_err = b->err.empty() ? std::string(tdks_status_string(s)) : b->err;
+    free_batch(b);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->st_body, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "stream creation";
+    return fail(TDKS_ERR_CUDA);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  b->ctx.assign(n_sys, nullptr);
+  for (int s = 0; s < n_sys; ++s) {
+    if (!(dt[s] > 0)) {
+      b->err = "system " + std::to_string(s) + ": dt must be > 0";
+      return fail(TDKS_ERR_ARG);
+    }
+    tdks_status st = tdks_create(&meshes[s], &systems[s], (void*)b->st, &b->ctx[s]);
+    if (st != TDKS_OK) {
+      b->err = "system " + std::to_string(s) + ": tdks_create failed";
+      return fail(st);
+    }
+    tdks_ctx* c = b->ctx[s];
+    if (!c->fdm_ok) {   // the in-graph Poisson CG needs the exact preconditioner
+      b->err = "system " + std::to_string(s) + ": an axis has more than 1024 interior nodes";
+      return fail(TDKS_ERR_ARG);
+    }
+  }
+  b->n_orb.resize(n_sys);
+  b->n_eblk.resize(n_sys);
+  b->n_rblk.resize(n_sys);
+  b->opb.assign(n_sys, 1);
+  b->dt.assign(dt, dt + n_sys);
+  b->psi.assign(n_sys, nullptr);
+  b->psi_half.assign(n_sys, nullptr);
+  b->Vw.assign(n_sys, nullptr);
+  b->kry.assign(n_sys, nullptr);
+  b->ev.assign(n_sys, nullptr);
+  b->apart.assign(n_sys, nullptr);
+  b->npart.assign(n_sys, nullptr);
+  b->h_half.resize(n_sys);
+  b->h_full.resize(n_sys);
+  std::vector<BOrb> orbs;
+  std::vector<BRow> rows;
+  std::map<int, int> deg_index;
+  for (int s = 0; s < n_sys; ++s) {
+    tdks_ctx* c = b->ctx[s];
+    const int no = c->n_orb;
+    b->n_orb[s] = no;
+    const size_t nv = (size_t)no * c->n_int;
+    const int nrows = c->Ni[1] * c->Ni[2];
+    b->n_rblk[s] = (int)std::max<long long>(1, std::min<long long>(nrows, (c->n_int + 4095) / 4096));
+    b->n_eblk[s] = (int)((c->n_elem + emax_of(c->P1) - 1) / emax_of(c->P1));
+    if (balloc(b, &b->psi[s], nv) || balloc(b, &b->psi_half[s], nv) ||
+        balloc(b, &b->Vw[s], nv * k_max) || balloc(b, &b->kry[s], (size_t)no) ||
+        balloc(b, (double2**)&b->ev[s], (size_t)no * c->n_elem * c->P1 * c->P1 * c->P1) ||
+        balloc(b, &b->apart[s], (size_t)no * c->n_elem) || balloc(b, &b->npart[s], (size_t)no * b->n_rblk[s]))
+      return fail(TDKS_ERR_NOMEM);
+    cudaMemset(b->psi[s], 0, nv * sizeof(double2));
+    BSys S;
+    std::memset(&S, 0, sizeof(S));
+    S.g = tdks_geom(c);
+    S.P1 = c->P1;
+    S.n_orb = no;
+    S.kmax = k_max;
+    S.n_eblk = b->n_eblk[s];
+    S.n_rblk = b->n_rblk[s];
+    S.n_int = c->n_int;
+    S.n_elem = c->n_elem;
+    S.in = b->psi[s];
+    S.vks = c->d_vks;
+    S.Vw = b->Vw[s];
+    S.kry = b->kry[s];
+    S.ev = b->ev[s];
+    S.apart = b->apart[s];
+    S.npart = b->npart[s];
+    S.dt = dt[s];
+    b->h_half[s] = S;
+    b->h_half[s].out = b->psi_half[s];
+    b->h_full[s] = S;
+    b->h_full[s].out = b->psi[s];
+    for (int o = 0; o < no; ++o) {
+      orbs.push_back(BOrb{s, o});
+      for (int r = 0; r < b->n_rblk[s]; ++r) rows.push_back(BRow{s, o, r, 0});
+    }
+    if (!deg_index.count(c->P1)) {
+      deg_index[c->P1] = (int)b->degs.size();
+      Deg d;
+      d.P1 = c->P1;
+      d.tab = prec == TDKS_FP32 ? (const void*)c->d_tabf : prec == TDKS_DF64 ? (const void*)c->d_tabdf
+                                                                             : (const void*)c->d_tab;
+      b->degs.push_back(d);
+    }
+  }
+  b->n_gorb = (int)orbs.size();
+  b->n_rows = (int)rows.size();
+  if (balloc(b, &b->d_half, n_sys) || balloc(b, &b->d_full, n_sys) || balloc(b, &b->d_orbs, orbs.size()) ||
+      balloc(b, &b->d_rows, rows.size()) || balloc(b, &b->d_rows_asm, rows.size()) ||
+      balloc(b, &b->d_ctrl, 8) || balloc(b, &b->d_dof, 1) ||
+      balloc(b, &b->d_dip, (size_t)b->dip_cap * n_sys * 3))
+    return fail(TDKS_ERR_NOMEM);
+  // assembly items: larger systems first, so their many row blocks start early
+  std::vector<BRow> rows_asm = rows;
+  std::stable_sort(rows_asm.begin(), rows_asm.end(), [&](const BRow& x, const BRow& y) {
+    return b->ctx[x.sys]->n_int / b->n_rblk[x.sys] > b->ctx[y.sys]->n_int / b->n_rblk[y.sys];
+  });
+  cudaMemcpy(b->d_orbs, orbs.data(), orbs.size() * sizeof(BOrb), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(BRow), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_rows_asm, rows_asm.data(), rows_asm.size() * sizeof(BRow), cudaMemcpyHostToDevice);
+  cudaMemset(b->d_ctrl, 0, 8 * sizeof(int));
+  cudaMemset(b->d_dof, 0, sizeof(unsigned long long));
+  for (Deg& d : b->degs)
+    if (build_degree(b, d, emax_of(d.P1)) != TDKS_OK) return fail(TDKS_ERR_CUDA);
+  if (upload_descriptors(b) != TDKS_OK) return fail(TDKS_ERR_CUDA);
+  const cudaError_t se = cudaDeviceSynchronize();
+  if (se != cudaSuccess) {
+    cudaGetLastError();
+    b->err = std::string("setup: ") + cudaGetErrorString(se);
+    return fail(TDKS_ERR_CUDA);
+  }
+  *out = b;
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_destroy(tdks_batch* b) {
+  if (!b) return TDKS_ERR_ARG;
+  cudaStreamSynchronize(b->st);
+  free_batch(b);
+  return TDKS_OK;
+}
+
+void* tdks_batch_stream(tdks_batch* b) { return b ? (void*)b->st : nullptr; }
+
+const char* tdks_batch_last_error(const tdks_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+tdks_status tdks_batch_sizes(const tdks_batch* b, int sys, int64_t* n_int, int64_t* n_elem, int* nq3,
+                             int* n_orb) {
+  if (!b || sys < 0 || sys >= b->n_sys) return TDKS_ERR_ARG;
+  const tdks_ctx* c = b->ctx[sys];
+  if (n_int) *n_int = c->n_int;
+  if (n_elem) *n_elem = c->n_elem;
+  if (nq3) *nq3 = (int)c->nq3;
+  if (n_orb) *n_orb = c->n_orb;
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_set_orbitals(tdks_batch* b, int sys, const double* psi_dev) {
+  if (!b || !psi_dev || sys < 0 || sys >= b->n_sys) return TDKS_ERR_ARG;
+  const size_t vb = (size_t)b->n_orb[sys] * b->ctx[sys]->n_int * sizeof(double2);
+  B_CU(b, cudaMemcpyAsync(b->psi[sys], psi_dev, vb, cudaMemcpyDeviceToDevice, b->st));
+  B_CU(b, cudaStreamSynchronize(b->st));
+  b->ready = false;
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_get_orbitals(tdks_batch* b, int sys, double* psi_dev) {
+  if (!b || !psi_dev || sys < 0 || sys >= b->n_sys) return TDKS_ERR_ARG;
+  const size_t vb = (size_t)b->n_orb[sys] * b->ctx[sys]->n_int * sizeof(double2);
+  B_CU(b, cudaMemcpyAsync(psi_dev, b->psi[sys], vb, cudaMemcpyDeviceToDevice, b->st));
+  B_CU(b, cudaStreamSynchronize(b->st));
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_kick(tdks_batch* b, const double* kappa, const double* dir) {
+  if (!b || !kappa || !dir) return TDKS_ERR_ARG;
+  for (int s = 0; s < b->n_sys; ++s)
+    B_TRY(b, ctx_try(b, b->ctx[s], launch_kick(b->ctx[s], b->psi[s], b->n_orb[s], kappa[s], dir + 3 * s)),
+          "kick");
+  B_CU(b, cudaStreamSynchronize(b->st));
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_init(tdks_batch* b, double* dip_host) {
+  if (!b) return TDKS_ERR_ARG;
+  for (int s = 0; s < b->n_sys; ++s) {
+    double d[3];
+    B_TRY(b, ctx_try(b, b->ctx[s], tdks_init_propagation(b->ctx[s], (const double*)b->psi[s], b->n_orb[s], d)),
+          "init");
+    if (dip_host) std::memcpy(dip_host + 3 * s, d, sizeof(d));
+  }
+  b->orbitals_set = true;
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out) {
+  if (!b || reps < 1) return TDKS_ERR_ARG;
+  if (!b->orbitals_set) return bfail(b, TDKS_ERR_ARG, "tune after tdks_batch_init (needs the orbitals)");
+  invalidate_graph(b);
+  // every orbital active at j = 0: the apply reads the orbitals themselves
+  B_CU(b, launch_bkry_init(b->d_full, b->d_orbs, b->n_gorb, 1.0, b->st));
+  B_CU(b, launch_bkry_prepare(b->d_full, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
+  b->tiles.clear();
+  for (Deg& d : b->degs) {
+    // classes of this degree by orbital count
+    std::map<int, std::vector<int>> cls;
+    for (int s = 0; s < b->n_sys; ++s)
+      if (b->ctx[s]->P1 == d.P1) cls[b->n_orb[s]].push_back(s);
+    // 1. elements per tile, one orbital per item
+    const int em = emax_of(d.P1);
+    std::vector<int> Es = {em, em - 1, (em + 1) / 2};
+    std::sort(Es.begin(), Es.end());
+    Es.erase(std::unique(Es.begin(), Es.end()), Es.end());
+    std::vector<int> one(b->n_sys, 1);
+    int bestE = em;
+    double bestT = 1e300;
+    for (int E : Es) {
+      if (E < 1) continue;
+      std::vector<BItem> items = make_items(b, d.P1, E, one, nullptr);
+      for (int s = 0; s < b->n_sys; ++s)
+        if (b->ctx[s]->P1 == d.P1) b->n_eblk[s] = (int)((b->ctx[s]->n_elem + E - 1) / E);
+      B_TRY(b, upload_descriptors(b), "tuning");
+      double t = 0;
+      B_TRY(b, time_apply(b, d, items, E, reps, &t), "tuning");
+      if (t < bestT) {
+        bestT = t;
+        bestE = E;
+      }
+    }
+    for (int s = 0; s < b->n_sys; ++s)
+      if (b->ctx[s]->P1 == d.P1) b->n_eblk[s] = (int)((b->ctx[s]->n_elem + bestE - 1) / bestE);
+    B_TRY(b, upload_descriptors(b), "tuning");
+    // 2. orbitals per item for each orbital-count class
+    for (auto& kv : cls) {
+      const int no = kv.first;
+      int bestB = 1;
+      double bT = 1e300;
+      for (int ob : {1, 2, 4, 8}) {
+        if (ob > no) break;
+        std::vector<int> opb(b->n_sys, ob);
+        std::vector<BItem> items = make_items(b, d.P1, bestE, opb, &kv.second);
+        double t = 0;
+        B_TRY(b, time_apply(b, d, items, bestE, reps, &t), "tuning");
+        if (t < bT) {
+          bT = t;
+          bestB = ob;
+        }
+      }
+      for (int s : kv.second) b->opb[s] = bestB;
+      b->tiles.push_back(tdks_tile_choice{d.P1 - 1, no, bestE, bestB, bT});
+    }
+    B_TRY(b, build_degree(b, d, bestE), "tuning");
+  }
+  B_TRY(b, upload_descriptors(b), "tuning");
+  if (out && n_out) {
+    const int n = std::min<int>(cap, (int)b->tiles.size());
+    for (int i = 0; i < n; ++i) out[i] = b->tiles[i];
+    *n_out = n;
+  } else if (n_out) {
+    *n_out = (int)b->tiles.size();
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host) {
+  if (!b || n_steps < 0) return TDKS_ERR_ARG;
+  if (!b->orbitals_set) return bfail(b, TDKS_ERR_ARG, "call tdks_batch_init first");
+  if (!b->exec) B_TRY(b, build_graph(b), "graph");
+  std::vector<double> buf;
+  int done = 0;
+  while (done < n_steps) {
+    const int chunk = std::min(b->dip_cap, n_steps - done);
+    B_CU(b, cudaMemsetAsync(b->d_ctrl + 3, 0, sizeof(int), b->st));
+    for (int k = 0; k < chunk; ++k) B_CU(b, cudaGraphLaunch(b->exec, b->st));
+    int ctrl[8];
+    B_CU(b, cudaMemcpyAsync(ctrl, b->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, b->st));
+    if (dip_host) {
+      buf.resize((size_t)chunk * b->n_sys * 3);
+      B_CU(b, cudaMemcpyAsync(buf.data(), b->d_dip, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    }
+    B_CU(b, cudaStreamSynchronize(b->st));
+    if (ctrl[2]) {
+      std::string m = "batched step failed:";
+      if (ctrl[2] & 1) m += " Lanczos failure (sub-step cap or non-finite);";
+      if (ctrl[2] & 2) m += " exponential loop reached its pass cap;";
+      if (ctrl[2] & 4) m += " Poisson CG not converged in the fixed iteration count;";
+      if (ctrl[2] & 8) m += " non-finite Poisson residual;";
+      return bfail(b, TDKS_ERR_NOT_CONVERGED, m);
+    }
+    if (dip_host) std::memcpy(dip_host + (size_t)done * b->n_sys * 3, buf.data(), buf.size() * sizeof(double));
+    done += chunk;
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_stats(tdks_batch* b, int64_t* dof_applies, int* k_max_seen, int reset) {
+  if (!b) return TDKS_ERR_ARG;
+  unsigned long long dof = 0;
+  int ctrl[8];
+  B_CU(b, cudaMemcpyAsync(&dof, b->d_dof, sizeof(dof), cudaMemcpyDeviceToHost, b->st));
+  B_CU(b, cudaMemcpyAsync(ctrl, b->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, b->st));
+  B_CU(b, cudaStreamSynchronize(b->st));
+  if (dof_applies) *dof_applies = (int64_t)dof;
+  if (k_max_seen) *k_max_seen = ctrl[4];
+  if (reset) {
+    B_CU(b, cudaMemsetAsync(b->d_dof, 0, sizeof(unsigned long long), b->st));
+    B_CU(b, cudaMemsetAsync(b->d_ctrl + 4, 0, sizeof(int), b->st));
+    B_CU(b, cudaStreamSynchronize(b->st));
+  }
+  return TDKS_OK;
+}
+
+}  // extern "C"

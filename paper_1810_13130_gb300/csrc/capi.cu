@@ -152,6 +152,25 @@ tdks_status check_orb(tdks_ctx* c, int n_orb) {
 
 }  // namespace
 
+// vhxc_of for stream capture (fixed-length Poisson CG, no host reads)
+tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter, int* err) {
+  const size_t nf = (size_t)(c->n_elem * c->nq3);
+  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
+  if (c->hartree) {
+    TDKS_TRY(hartree_graph(c, c->d_rho, c->d_vh, n_iter, err));
+  } else {
+    TDKS_CU(c, cudaMemsetAsync(c->d_vh, 0, nf * sizeof(double), c->stream));
+  }
+  if (c->xc) {
+    TDKS_TRY(launch_xc(c, c->d_rho, c->d_vtmp));
+    TDKS_TRY(launch_combine(c, out, c->d_vh, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, nullptr));
+  } else {
+    TDKS_CU(c, cudaMemcpyAsync(out, c->d_vh, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return TDKS_OK;
+}
+
+
 extern "C" {
 
 const char* tdks_status_string(int s) {

@@ -48,35 +48,24 @@ struct Cfg {
 //   y-line:  R += cy W W (Kq u~)_y;  z-line: r = R + cz W W (Kq u~)_z
 //   backward z -> y -> x (B^T), scatter-add of the x-line with the Loewdin scale.
 // ---------------------------------------------------------------------------
-// Register budget of the element kernel: at most 128 registers, so that two CTAs
-// (16 warps) share an SM.
-template <int P1, typename T>
-__global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ tab,
-                                              const double* __restrict__ vks, ApplyArgs a,
-                                              int orb_per_cta, Cx<T>* __restrict__ ev) {
+// Element body shared by the single-system and the batched kernels: the threads
+// of row threadIdx.y handle element eidx (P1 x P1 lines each) for the orbitals
+// [o_begin, o_end) that orb(o, in, sc) accepts (in: the orbital's input vector,
+// sc: its scale); results go to ev, alpha partials to part[o][pslot].
+// Shared tables (sB, sBT, sK, sw) must be loaded and synchronized by the caller.
+template <int P1, typename T, class OrbFn>
+__device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const T* sBT, const T* sK,
+                                               const T* sw, Cx<T>* S1, Cx<T>* S2, double* red,
+                                               const double* __restrict__ vks, long long eidx,
+                                               int o_begin, int o_end, OrbFn orb,
+                                               Cx<T>* __restrict__ ev, double* part,
+                                               int64_t part_stride, long long pslot) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
-  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   typedef Cx<T> V;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[8];
-  T* sB = reinterpret_cast<T*>(smem);
-  T* sBT = sB + CS;
-  T* sK = sBT + CS;
-  T* sw = sK + CS;
-  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
-  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
-  V* S2 = S1 + P3;
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int nthr = blockDim.x * blockDim.y;
-  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
-  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
-  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
   const bool valid = plain_elem(g, eidx, ex, ey, ez);
   const long long n_elem = (long long)g.nx * g.ny * g.nz;
-  __syncthreads();
-
   T fx = from_d<T>(0.0), fy = from_d<T>(0.0), fz = from_d<T>(0.0);
   T vx[P1];
 #pragma unroll
@@ -109,15 +98,10 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
     gsc[c] = from_d<T>((inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0);
   }
 
-  for (int oo = 0; oo < orb_per_cta; ++oo) {
-    const int o = blockIdx.y * orb_per_cta + oo;
-    if (o >= a.n_orb) break;
+  for (int o = o_begin; o < o_end; ++o) {
+    const double2* in = nullptr;
     double sc = 1.0;
-    if (a.kry) {
-      if (a.kry[o].status != KRY_ACTIVE) continue;
-      sc = a.kry[o].s[a.kj];
-    }
-    const double2* in = a.in_base + (long long)o * a.in_stride;
+    if (!orb(o, in, sc)) continue;
     V col[P1], t[P1];
     T scT;
     if constexpr (kF32) scT = d2f_bits(sc);
@@ -201,12 +185,50 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
     load_line(col, S2 + v * P2 + u * P1, 1);
     cs_apply<P1>(sBT, col, t);
     if (valid) store_line(t, ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1, 1);
-    if (a.part) {
+    if (part) {
       const double s = block_sum(apart, red);
-      if (tid == 0) a.part[(long long)o * a.part_stride + blockIdx.x] = s;
+      if (threadIdx.x + blockDim.x * threadIdx.y == 0) part[(long long)o * part_stride + pslot] = s;
     }
     __syncthreads();
   }
+}
+
+// Register budget of the element kernels: at most 128 registers, so that two CTAs
+// (16 warps) share an SM.
+template <int P1, typename T>
+__global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ tab,
+                                              const double* __restrict__ vks, ApplyArgs a,
+                                              int orb_per_cta, Cx<T>* __restrict__ ev) {
+  constexpr int P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  typedef Cx<T> V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  T* sB = reinterpret_cast<T*>(smem);
+  T* sBT = sB + CS;
+  T* sK = sBT + CS;
+  T* sw = sK + CS;
+  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  V* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  __syncthreads();
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const int o0 = blockIdx.y * orb_per_cta;
+  const int o1 = min(o0 + orb_per_cta, a.n_orb);
+  auto orb = [&](int o, const double2*& in, double& sc) -> bool {
+    if (a.kry) {
+      if (a.kry[o].status != KRY_ACTIVE) return false;
+      sc = a.kry[o].s[a.kj];
+    }
+    in = a.in_base + (long long)o * a.in_stride;
+    return true;
+  };
+  hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
+                        a.part_stride, blockIdx.x);
 }
 
 // alpha_j = sum of the element partials (fixed order), for the active orbitals
@@ -246,33 +268,20 @@ __device__ __forceinline__ int node_elems(int I, int p, int n, int* e, int* loc)
 // Assembly by gathering: every interior node sums its (at most 8) element-local
 // contributions in a fixed order and applies the Loewdin scale.  With `lanczos`
 // the three-term update w = Hbar q_j - alpha_j q_j - beta_{j-1} q_{j-1} is fused
-// and the per-block partials of ||w||^2 are written.
+// (ca = alpha_j s_j, cb = beta_{j-1} s_{j-1}) and the sum of |w|^2 over the rows
+// r0, r0 + rstride, ... handled here is returned.
 template <typename T>
-__global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* __restrict__ ev,
-                                                  ApplyArgs a) {
-  __shared__ double red[4];
-  const int o = blockIdx.y;
-  double ca = 0.0, cb = 0.0;
-  if (a.kry) {
-    const KryOrb& K = a.kry[o];
-    if (K.status != KRY_ACTIVE) return;
-    if (a.lanczos) {
-      ca = K.alpha[a.kj] * K.s[a.kj];
-      cb = a.kj > 0 ? K.beta[a.kj - 1] * K.s[a.kj - 1] : 0.0;
-    }
-  }
+__device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<T>* __restrict__ evo,
+                                                const double2* qj, const double2* qm,
+                                                double2* out, double ca, double cb, int lanczos,
+                                                int accumulate, int r0, int rstride) {
   const int P2 = P1 * P1;
   const long long P3 = (long long)P2 * P1;
-  const long long n_elem = (long long)g.nx * g.ny * g.nz;
-  const Cx<T>* evo = ev + (long long)o * n_elem * P3;
-  const double2* qj = a.in_base + (long long)o * a.in_stride;
-  const double2* qm = a.vm_base ? a.vm_base + (long long)o * a.vm_stride : nullptr;
-  double2* out = a.out_base + (long long)o * a.out_stride;
   constexpr bool kF32 = std::is_same<T, float>::value;
   constexpr bool kDF = std::is_same<T, Df>::value;
   const int rows = g.niy * g.niz;
   double acc = 0.0;
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+  for (int r = r0; r < rows; r += rstride) {
     const int J = r % g.niy + 1, K = r / g.niy + 1;
     int ey[2], by[2], ez[2], bz[2], ex[2], bx[2];
     const int ny = node_elems(J, g.p, g.ny, ey, by);
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
         const double f = g.s[0][I] * syz;
         w = make_double2(f * re, f * im);
       }
-      if (a.lanczos) {
+      if (lanczos) {
         const double2 x = qj[idx];
         w.x = fma(-ca, x.x, w.x);
         w.y = fma(-ca, x.y, w.y);
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
         }
         acc = fma(w.x, w.x, fma(w.y, w.y, acc));
       }
-      if (a.accumulate) {
+      if (accumulate) {
         const double2 o2 = out[idx];
         w.x += o2.x;
         w.y += o2.y;
@@ -333,10 +342,131 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
       out[idx] = w;
     }
   }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* __restrict__ ev,
+                                                  ApplyArgs a) {
+  __shared__ double red[4];
+  const int o = blockIdx.y;
+  double ca = 0.0, cb = 0.0;
+  if (a.kry) {
+    const KryOrb& K = a.kry[o];
+    if (K.status != KRY_ACTIVE) return;
+    if (a.lanczos) {
+      ca = K.alpha[a.kj] * K.s[a.kj];
+      cb = a.kj > 0 ? K.beta[a.kj - 1] * K.s[a.kj - 1] : 0.0;
+    }
+  }
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  const Cx<T>* evo = ev + (long long)o * n_elem * P1 * P1 * P1;
+  const double2* qj = a.in_base + (long long)o * a.in_stride;
+  const double2* qm = a.vm_base ? a.vm_base + (long long)o * a.vm_stride : nullptr;
+  double2* out = a.out_base + (long long)o * a.out_stride;
+  const double acc = assemble_rows<T>(g, P1, evo, qj, qm, out, ca, cb, a.lanczos, a.accumulate,
+                                      blockIdx.x, gridDim.x);
   if (a.npart) {
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) a.npart[(long long)o * a.npart_stride + blockIdx.x] = s;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched apply: a persistent grid walks the work list of one degree class.
+// Item (sys, eblk, o0, o1): elements [eblk E, eblk E + E) of system sys for the
+// orbitals o0..o1-1 that are in the Lanczos recurrence; each orbital reads its own
+// current basis vector V_j (j = K.k): the exponential's start vector for j = 0
+// (input or, after a sub-step, output), the workspace otherwise.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ const double2* bvec(const BSys& S, const KryOrb& K, int o, int j) {
+  if (j == 0) return (K.nsub == 0 ? S.in : S.out) + (long long)o * S.n_int;
+  return S.Vw + ((long long)o * S.kmax + (j - 1)) * S.n_int;
+}
+
+template <int P1, typename T>
+__global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ sys,
+                                                    const BItem* __restrict__ items, int n_items,
+                                                    const T* __restrict__ tab) {
+  constexpr int P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  typedef Cx<T> V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  T* sB = reinterpret_cast<T*>(smem);
+  T* sBT = sB + CS;
+  T* sK = sBT + CS;
+  T* sw = sK + CS;
+  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  V* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  __syncthreads();
+  // the current item's system descriptor is staged in shared memory: its fields are
+  // re-read where used instead of occupying registers across the element body
+  __shared__ BSys sS;
+  __shared__ BItem sW;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __syncthreads();
+    if (tid == 0) sW = items[it];
+    __syncthreads();
+    for (int i = tid; i < (int)(sizeof(BSys) / 8); i += nthr)
+      reinterpret_cast<long long*>(&sS)[i] = reinterpret_cast<const long long*>(&sys[sW.sys])[i];
+    __syncthreads();
+    const BItem w = sW;
+    const BSys& S = sS;
+    const Geom& g = S.g;
+    const long long eidx = (long long)w.eblk * blockDim.y + threadIdx.y;
+    auto orb = [&](int o, const double2*& in, double& sc) -> bool {
+      const KryOrb& K = S.kry[o];
+      if (K.status != KRY_ACTIVE) return false;
+      const int j = K.k;
+      in = bvec(S, K, o, j);
+      sc = K.s[j];
+      return true;
+    };
+    hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
+                          static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk);
+  }
+}
+
+// alpha_j from the element partials (fixed order), one block per orbital
+__global__ void k_balpha(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs) {
+  __shared__ double red[8];
+  const BOrb b = orbs[blockIdx.x];
+  const BSys& S = sys[b.sys];
+  KryOrb& K = S.kry[b.o];
+  if (K.status != KRY_ACTIVE) return;
+  const double* part = S.apart + (long long)b.o * S.n_eblk;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < S.n_eblk; k += blockDim.x) v += part[k];
+  const double s = block_sum(v, red);
+  if (threadIdx.x == 0) K.alpha[K.k] = s;
+}
+
+// gather assembly with the three-term update, one block per (system, orbital, row block)
+template <typename T>
+__global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
+                                                   const BRow* __restrict__ rows) {
+  __shared__ double red[4];
+  const BRow w = rows[blockIdx.x];
+  const BSys& S = sys[w.sys];
+  const KryOrb& K = S.kry[w.o];
+  if (K.status != KRY_ACTIVE) return;
+  const int j = K.k;
+  const double ca = K.alpha[j] * K.s[j];
+  const double cb = j > 0 ? K.beta[j - 1] * K.s[j - 1] : 0.0;
+  const double2* qj = bvec(S, K, w.o, j);
+  const double2* qm = j > 0 ? bvec(S, K, w.o, j - 1) : nullptr;
+  double2* out = S.Vw + ((long long)w.o * S.kmax + j) * S.n_int;
+  const Geom g = S.g;
+  const Cx<T>* evo = static_cast<const Cx<T>*>(S.ev) + (long long)w.o * S.n_elem * S.P1 * S.P1 * S.P1;
+  const double acc = assemble_rows<T>(g, S.P1, evo, qj, qm, out, ca, cb, 1, 0, w.rblk, S.n_rblk);
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) S.npart[(long long)w.o * S.n_rblk + w.rblk] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1015,4 +1145,97 @@ tdks_status launch_cross(tdks_ctx* c, const double2* mu, const double2* phi, int
 tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q) {
   TDKS_DISPATCH(c->P1, (density_t<P1>(c, psi, n_orb, rho_q)));
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
+}
+
+// ---- batched apply launchers ------------------------------------------------
+template <int P1, typename T>
+static size_t hbar_batch_smem_t(int E) {
+  constexpr int P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
+}
+
+template <int P1>
+static size_t hbar_batch_smem_p(int prec, int E) {
+  if (prec == TDKS_FP32) return hbar_batch_smem_t<P1, float>(E);
+  if (prec == TDKS_DF64) return hbar_batch_smem_t<P1, Df>(E);
+  return hbar_batch_smem_t<P1, double>(E);
+}
+
+size_t hbar_batch_smem(int P1, int prec, int E) {
+  switch (P1) {
+    case 2: return hbar_batch_smem_p<2>(prec, E);
+    case 3: return hbar_batch_smem_p<3>(prec, E);
+    case 4: return hbar_batch_smem_p<4>(prec, E);
+    case 5: return hbar_batch_smem_p<5>(prec, E);
+    case 6: return hbar_batch_smem_p<6>(prec, E);
+    case 7: return hbar_batch_smem_p<7>(prec, E);
+    case 8: return hbar_batch_smem_p<8>(prec, E);
+    case 9: return hbar_batch_smem_p<9>(prec, E);
+    default: return 0;
+  }
+}
+
+template <int P1, typename T>
+static cudaError_t hbar_batch_launch_t(const BSys* sys, const BItem* items, int n_items, int E,
+                                       int grid, const void* tab, cudaStream_t st, int* occ) {
+  const size_t smem = hbar_batch_smem_t<P1, T>(E);
+  // the kernel also holds ~330 B of static shared memory: opt in for any large size
+  cudaError_t e = cudaFuncSetAttribute(k_hbar_batch<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_hbar_batch<P1, T>, Cfg<P1>::P2 * E, smem);
+  if (n_items <= 0) return cudaSuccess;
+  k_hbar_batch<P1, T><<<grid, dim3(Cfg<P1>::P2, E), smem, st>>>(sys, items, n_items,
+                                                               static_cast<const T*>(tab));
+  return cudaGetLastError();
+}
+
+template <int P1>
+static cudaError_t hbar_batch_p(int prec, const BSys* sys, const BItem* items, int n_items, int E,
+                                int grid, const void* tab, cudaStream_t st, int* occ) {
+  if (E < 1 || Cfg<P1>::P2 * E > 256) return cudaErrorInvalidValue;
+  if (prec == TDKS_FP32) return hbar_batch_launch_t<P1, float>(sys, items, n_items, E, grid, tab, st, occ);
+  if (prec == TDKS_DF64) return hbar_batch_launch_t<P1, Df>(sys, items, n_items, E, grid, tab, st, occ);
+  return hbar_batch_launch_t<P1, double>(sys, items, n_items, E, grid, tab, st, occ);
+}
+
+static cudaError_t hbar_batch_dispatch(int P1, int prec, const BSys* sys, const BItem* items,
+                                       int n_items, int E, int grid, const void* tab,
+                                       cudaStream_t st, int* occ) {
+  switch (P1) {
+    case 2: return hbar_batch_p<2>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 3: return hbar_batch_p<3>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 4: return hbar_batch_p<4>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 5: return hbar_batch_p<5>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 6: return hbar_batch_p<6>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 7: return hbar_batch_p<7>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 8: return hbar_batch_p<8>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 9: return hbar_batch_p<9>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t hbar_batch_occupancy(int P1, int prec, int E, int* blocks_per_sm) {
+  *blocks_per_sm = 0;
+  return hbar_batch_dispatch(P1, prec, nullptr, nullptr, 0, E, 0, nullptr, nullptr, blocks_per_sm);
+}
+
+cudaError_t launch_hbar_batch(int P1, int prec, const BSys* sys, const BItem* items, int n_items,
+                              int E, int grid, const void* tab, cudaStream_t st) {
+  return hbar_batch_dispatch(P1, prec, sys, items, n_items, E, grid, tab, st, nullptr);
+}
+
+cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st) {
+  if (n_orbs <= 0) return cudaSuccess;
+  k_balpha<<<n_orbs, 256, 0, st>>>(sys, orbs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  if (prec == TDKS_FP32) k_bassemble<float><<<n_rows, 128, 0, st>>>(sys, rows);
+  else if (prec == TDKS_DF64) k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
+  else k_bassemble<double><<<n_rows, 128, 0, st>>>(sys, rows);
+  return cudaGetLastError();
 }

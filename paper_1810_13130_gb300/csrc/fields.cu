@@ -192,6 +192,20 @@ __global__ void k_sum_parts3(const double* part, int nb, double* out) {
   }
 }
 
+// d = sum of the partials, written to base + (*step) * stride (step counter on the device)
+__global__ void k_sum_parts3_at(const double* part, int nb, double* base, const int* step,
+                                int64_t stride) {
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int k = 0; k < nb; ++k) s += part[threadIdx.x * nb + k];
+    base[(long long)(*step) * stride + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_counter_add(int* counter, int inc) {
+  if (threadIdx.x == 0) *counter += inc;
+}
+
 __global__ void k_kick(const double* cx, const double* cy, const double* cz, int nix, int niy,
                        long long n, int n_orb, double2* psi, double kappa, double dx, double dy,
                        double dz) {
@@ -291,4 +305,23 @@ tdks_status launch_kick(tdks_ctx* c, double2* psi, int n_orb, double kappa, cons
   c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
+}
+
+// run_dipole without the host read, for stream capture
+tdks_status dipole_graph(tdks_ctx* c, const double* rho, double* base, const int* step,
+                         int64_t step_stride) {
+  const long long n = c->n_elem * c->nq3;
+  const int nb = vec_grid(n);
+  double* part = c->d_part;
+  k_dipole_part<<<nb, kVecThreads, 0, c->stream>>>(tdks_geom(c), c->d_tab + tab_off_eta(c->P1),
+                                                   c->d_tab + tab_off_w(c->P1), c->P1, n, rho, part, 1);
+  k_sum_parts3_at<<<1, 32, 0, c->stream>>>(part, nb, base, step, step_stride);
+  c->n_launch += 2;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+cudaError_t launch_counter_add(int* counter, int inc, cudaStream_t st) {
+  k_counter_add<<<1, 32, 0, st>>>(counter, inc);
+  return cudaGetLastError();
 }

@@ -256,17 +256,11 @@ __device__ bool cheb_exp_signed(int m, double tau, ChebWork& W) {
 }
 
 // One warp per orbital: beta_j, small exponential, a-posteriori estimate, decision.
-__global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double* npart,
-                          int64_t npstride, int nb) {
-  __shared__ ChebWork W;
-  const int o = blockIdx.x;
-  const int lane = threadIdx.x;
-  KryOrb& K = kry[o];
-  if (K.status != KRY_ACTIVE) return;
-  double v = 0.0;
-  for (int k = lane; k < nb; k += 32) v += npart[(long long)o * npstride + k];
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const double beta = sqrt(v);
+// Decision after the apply of basis vector j (beta = ||w||): small exponential,
+// a-posteriori estimate, and continue / converged / sub-step / failed.  Called
+// by one full warp.
+__device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, ChebWork& W) {
+  const int lane = threadIdx.x & 31;
   const int m = j + 1;
   for (int i = lane; i < m; i += 32) {
     W.a[i] = K.alpha[i];
@@ -318,6 +312,19 @@ __global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double
   }
 }
 
+__global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double* npart,
+                          int64_t npstride, int nb) {
+  __shared__ ChebWork W;
+  const int o = blockIdx.x;
+  const int lane = threadIdx.x;
+  KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  double v = 0.0;
+  for (int k = lane; k < nb; k += 32) v += npart[(long long)o * npstride + k];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  kry_decide(K, j, kmax, tol, sqrt(v), W);
+}
+
 // out = ||psi|| sum_j y_j s_j V_j
 __global__ void k_kry_recomb(long long n, double2* out, int64_t so, const double2* V0, int64_t s0,
                              const double2* Vw, int64_t sw, int kmax, const KryOrb* kry) {
@@ -364,6 +371,188 @@ __global__ void k_kry_after(KryOrb* kry, int n_orb) {
       K.status = (K.nsub >= TDKS_MAX_SUBSTEPS) ? KRY_FAILED : KRY_ACTIVE;
     }
   }
+}
+
+// ---- batched exponential: per-orbital state machine over many systems --------
+// RESTART -> (norm) ACTIVE -> (apply, decide) ACTIVE | CONVERGED | SUBSTEP | FAILED;
+// CONVERGED/SUBSTEP -> (recombine) DONE | RESTART.  One pass of the loop body
+// advances every orbital by one step of this machine.
+__device__ __forceinline__ const double2* bcur(const BSys& S, const KryOrb& K, int o) {
+  return (K.nsub == 0 ? S.in : S.out) + (long long)o * S.n_int;
+}
+
+__global__ void k_bkry_init(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n,
+                            double factor) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const BOrb b = orbs[g];
+  const BSys& S = sys[b.sys];
+  KryOrb& K = S.kry[b.o];
+  K.t_rem = factor * S.dt;
+  K.tau_sub = 0.0;
+  K.status = KRY_RESTART;
+  K.k = 0;
+  K.k_total = 0;
+  K.nsub = 0;
+  K.applies = 0;
+  K.pad = 0;
+}
+
+// partial ||v||^2 of the (re)starting orbitals, one block per chunk of n_int / n_rblk entries
+__global__ void k_bnorm_part(const BSys* __restrict__ sys, const BRow* __restrict__ rows) {
+  __shared__ double red[kThreads / 32];
+  const BRow w = rows[blockIdx.x];
+  const BSys& S = sys[w.sys];
+  const KryOrb& K = S.kry[w.o];
+  if (K.status != KRY_RESTART) return;
+  const double2* v = bcur(S, K, w.o);
+  const long long chunk = (S.n_int + S.n_rblk - 1) / S.n_rblk;
+  const long long i1 = min(S.n_int, (w.rblk + 1) * chunk);
+  double acc = 0.0;
+  for (long long i = w.rblk * chunk + threadIdx.x; i < i1; i += blockDim.x) {
+    const double2 a = v[i];
+    acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+  }
+  const double t = block_reduce_sum(acc, red);
+  if (threadIdx.x == 0) S.npart[(long long)w.o * S.n_rblk + w.rblk] = t;
+}
+
+__global__ void k_bkry_start(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs) {
+  __shared__ double red[kThreads / 32];
+  const BOrb b = orbs[blockIdx.x];
+  const BSys& S = sys[b.sys];
+  KryOrb& K = S.kry[b.o];
+  if (K.status != KRY_RESTART) return;
+  const double t = sum_fixed(S.npart + (long long)b.o * S.n_rblk, S.n_rblk, red);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(t);
+    K.nrm = nrm;
+    K.k = 0;
+    if (!isfinite(nrm)) {
+      K.status = KRY_FAILED;
+    } else if (nrm == 0.0) {
+      K.status = KRY_CONVERGED;   // exp of the zero vector: recombination writes zeros
+      K.tau_sub = K.t_rem;
+    } else {
+      K.s[0] = 1.0 / nrm;
+      K.status = KRY_ACTIVE;
+    }
+  }
+}
+
+// beta_j, small exponential and decision: one warp per orbital, j = K.k
+__global__ void k_bkry_exp(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, double tol) {
+  __shared__ ChebWork W;
+  const BOrb b = orbs[blockIdx.x];
+  const BSys& S = sys[b.sys];
+  KryOrb& K = S.kry[b.o];
+  if (K.status != KRY_ACTIVE) return;
+  const int lane = threadIdx.x;
+  const double* np = S.npart + (long long)b.o * S.n_rblk;
+  double v = 0.0;
+  for (int k = lane; k < S.n_rblk; k += 32) v += np[k];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int j = K.k;
+  kry_decide(K, j, S.kmax, tol, sqrt(v), W);
+}
+
+// out = ||psi|| sum_j y_j s_j V_j of converged / sub-stepped orbitals, one block per chunk
+__global__ void k_brecomb(const BSys* __restrict__ sys, const BRow* __restrict__ rows) {
+  __shared__ double cr[TDKS_KMAX], ci[TDKS_KMAX];
+  const BRow w = rows[blockIdx.x];
+  const BSys& S = sys[w.sys];
+  const KryOrb& K = S.kry[w.o];
+  const int st = K.status;
+  if (st != KRY_CONVERGED && st != KRY_SUBSTEP) return;
+  const int m = K.k;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double f = K.nrm * K.s[j];
+    cr[j] = f * K.yre[j];
+    ci[j] = f * K.yim[j];
+  }
+  __syncthreads();
+  const long long n = S.n_int;
+  const double2* v0 = bcur(S, K, w.o);
+  const double2* vw = S.Vw + (long long)w.o * S.kmax * n;
+  double2* dst = S.out + (long long)w.o * n;
+  const long long chunk = (n + S.n_rblk - 1) / S.n_rblk;
+  const long long i1 = min(n, (w.rblk + 1) * chunk);
+  for (long long i = w.rblk * chunk + threadIdx.x; i < i1; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
+      re = fma(cr[j], v.x, fma(-ci[j], v.y, re));
+      im = fma(cr[j], v.y, fma(ci[j], v.x, im));
+    }
+    dst[i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_bkry_after(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const BOrb b = orbs[g];
+  KryOrb& K = sys[b.sys].kry[b.o];
+  if (K.status == KRY_CONVERGED || K.status == KRY_SUBSTEP) {
+    K.k_total += K.k;
+    K.nsub += 1;
+    if (K.k > K.pad) K.pad = K.k;
+    if (K.status == KRY_CONVERGED) {
+      K.t_rem = 0.0;
+      K.status = KRY_DONE;
+    } else {
+      K.t_rem -= K.tau_sub;
+      K.status = (K.nsub >= TDKS_MAX_SUBSTEPS) ? KRY_FAILED : KRY_RESTART;
+    }
+  }
+}
+
+__global__ void k_bloop_begin(cudaGraphConditionalHandle h, int* iter) {
+  if (threadIdx.x == 0) {
+    *iter = 0;
+    cudaGraphSetConditional(h, 1u);
+  }
+}
+
+// Loop condition: continue while some orbital is still in the recurrence, none
+// failed and the pass count is below the cap (bit 1 of *err: failure, bit 2: cap).
+__global__ void k_bloop_control(cudaGraphConditionalHandle h, const BSys* __restrict__ sys,
+                                const BOrb* __restrict__ orbs, int n, int* iter, int cap, int* err) {
+  __shared__ int s_act, s_fail;
+  if (threadIdx.x == 0) {
+    s_act = 0;
+    s_fail = 0;
+  }
+  __syncthreads();
+  int act = 0, fail = 0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const BOrb b = orbs[g];
+    const int st = sys[b.sys].kry[b.o].status;
+    act |= (st == KRY_RESTART || st == KRY_ACTIVE);
+    fail |= (st == KRY_FAILED);
+  }
+  if (act) atomicOr(&s_act, 1);
+  if (fail) atomicOr(&s_fail, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = *iter + 1;
+    *iter = it;
+    if (s_fail) atomicOr(err, 1);
+    if (s_act && !s_fail && it >= cap) atomicOr(err, 2);
+    cudaGraphSetConditional(h, (s_act && !s_fail && it < cap) ? 1u : 0u);
+  }
+}
+
+// orbital-vector applies x interior DoFs and the largest Krylov dimension of the pass
+__global__ void k_bkry_stats(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n,
+                             unsigned long long* dof_applies, int* kseen) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const BOrb b = orbs[g];
+  const BSys& S = sys[b.sys];
+  const KryOrb& K = S.kry[b.o];
+  atomicAdd(dof_applies, (unsigned long long)K.applies * (unsigned long long)S.n_int);
+  atomicMax(kseen, K.pad);
 }
 
 int grid_for(long long n) {
@@ -509,4 +698,46 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
   if (applies) *applies = napp;
   if (nsub) *nsub = ns;
   return TDKS_OK;
+}
+
+// ---- batched exponential launchers ------------------------------------------
+cudaError_t launch_bkry_init(const BSys* sys, const BOrb* orbs, int n, double factor, cudaStream_t st) {
+  k_bkry_init<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n, factor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkry_prepare(const BSys* sys, const BOrb* orbs, int n, const BRow* rows, int n_rows,
+                                cudaStream_t st) {
+  k_bnorm_part<<<n_rows, kThreads, 0, st>>>(sys, rows);
+  k_bkry_start<<<n, kThreads, 0, st>>>(sys, orbs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n, double tol, cudaStream_t st) {
+  k_bkry_exp<<<n, 32, 0, st>>>(sys, orbs, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n, const BRow* rows, int n_rows,
+                               cudaStream_t st) {
+  k_brecomb<<<n_rows, kThreads, 0, st>>>(sys, rows);
+  k_bkry_after<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, cudaStream_t st) {
+  k_bloop_begin<<<1, 32, 0, st>>>(h, iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs, int n,
+                                 int* iter, int cap, int* err, cudaStream_t st) {
+  k_bloop_control<<<1, kThreads, 0, st>>>(h, sys, orbs, n, iter, cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n, unsigned long long* dof_applies,
+                              int* kseen, cudaStream_t st) {
+  k_bkry_stats<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n, dof_applies, kseen);
+  return cudaGetLastError();
 }

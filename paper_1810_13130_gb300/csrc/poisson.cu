@@ -358,6 +358,20 @@ void axis_gemm(tdks_ctx* c, int axis, bool forward, const double* in, double* ou
 }
 
 // z = S D^-1 S^T r  (exact inverse of the separable stiffness)
+// End of a fixed-length CG: zero right-hand side -> x = 0; not converged or
+// non-finite -> error bits (4: iteration cap, 8: non-finite).
+__global__ void k_cg_graph_end(long long n, double* x, const CgState* cg, int* err) {
+  const int failed = cg->failed;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (failed == 1) atomicOr(err, 8);
+    else if (failed != 3 && !cg->done) atomicOr(err, 4);
+  }
+  if (failed != 3) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = 0.0;
+}
+
 void fdm_apply(tdks_ctx* c, const double* r, double* z, const CgState* cg) {
   const long long n = c->n_int;
   axis_gemm(c, 0, true, r, c->d_t1, cg);
@@ -486,6 +500,54 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
   TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
   TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
   TDKS_TRY(run_cg_solve(c, c->d_b, c->d_phi, iters));
+  TDKS_TRY(launch_interp(c, c->d_phi, vh_q));
+  return TDKS_OK;
+}
+
+// The CG of run_cg_solve with a fixed number of iterations and no host
+// synchronization, for stream capture: every kernel of an iteration returns at
+// once after convergence, so extra iterations cost launches only.  Needs the
+// fast-diagonalization preconditioner (one or two iterations); an unconverged
+// solve sets bit 4 of *err.
+tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err) {
+  if (!(c->cg_precond == 0 && c->fdm_ok))
+    return tdks_fail(c, TDKS_ERR_ARG, "graph CG needs the fast-diagonalization preconditioner");
+  const long long n = c->n_int;
+  const int nb = grid_for(n);
+  const int sbpc = stiff_blocks_per_color(c);
+  double* part_pAp = c->d_part;
+  double* part_vec = c->d_part + 8 * (int64_t)sbpc;
+  CgState* cg = c->d_cg;
+  TDKS_CU(c, cudaMemsetAsync(c->d_Ap, 0, n * sizeof(double), c->stream));
+  TDKS_TRY(launch_stiffness(c, x, c->d_Ap, nullptr, nullptr));
+  k_cg_init<<<nb, kThreads, 0, c->stream>>>(n, b, c->d_Ap, c->d_r, part_vec);
+  k_cg_init_fin<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, cg);
+  auto precondition = [&]() {
+    fdm_apply(c, c->d_r, c->d_z, cg);
+    k_dot_part<<<nb, kThreads, 0, c->stream>>>(n, c->d_r, c->d_z, part_vec, cg);
+    k_cg_fin_rz<<<1, kThreads, 0, c->stream>>>(part_vec, nb, cg);
+    k_cg_dir<<<nb, kThreads, 0, c->stream>>>(n, c->d_z, c->d_pv, cg);
+    k_cg_clear_first<<<1, 1, 0, c->stream>>>(cg);
+  };
+  precondition();
+  for (int it = 0; it < n_iter; ++it) {
+    TDKS_CU(c, cudaMemsetAsync(c->d_Ap, 0, n * sizeof(double), c->stream));
+    TDKS_TRY(launch_stiffness(c, c->d_pv, c->d_Ap, part_pAp, cg));
+    k_cg_update<<<nb, kThreads, 0, c->stream>>>(n, part_pAp, 8 * sbpc, x, c->d_r, c->d_pv, c->d_Ap,
+                                                part_vec, cg);
+    k_cg_fin_rr<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, c->cg_maxit, cg);
+    precondition();
+  }
+  k_cg_graph_end<<<nb, kThreads, 0, c->stream>>>(n, x, cg, err);
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err) {
+  const long long n = c->n_int;
+  TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
+  TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
+  TDKS_TRY(cg_solve_graph(c, c->d_b, c->d_phi, n_iter, err));
   TDKS_TRY(launch_interp(c, c->d_phi, vh_q));
   return TDKS_OK;
 }

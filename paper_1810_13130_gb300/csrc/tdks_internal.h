@@ -245,3 +245,63 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
 
 // reduction helper used by several files
 tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);
+
+// ---------------------------------------------------------------------------
+// Batched engine: many independent systems advanced by the same launches.
+// Every orbital keeps its own Lanczos state (KryOrb); its current Krylov index is
+// K.k, so systems and orbitals progress independently inside one device loop.
+// ---------------------------------------------------------------------------
+enum { KRY_RESTART = 4 };      // ||v|| needed before the recurrence (re)starts
+
+struct BSys {
+  Geom g;
+  int P1, n_orb, kmax;
+  int n_eblk;                  // element blocks of the apply (alpha partials per orbital)
+  int n_rblk;                  // row blocks of assembly / norms / recombination
+  int pad0;
+  long long n_int, n_elem;
+  const double2* in;           // exponential input [n_orb][n_int]
+  double2* out;                // output [n_orb][n_int] (may equal in)
+  const double* vks;           // V_KS at the Gauss points
+  double2* Vw;                 // Krylov vectors V_1 .. V_kmax [n_orb][kmax][n_int]
+  KryOrb* kry;                 // [n_orb]
+  void* ev;                    // element results [n_orb][n_elem][P1^3] (contraction type)
+  double* apart;               // alpha partials [n_orb][n_eblk]
+  double* npart;               // norm partials [n_orb][n_rblk]
+  double dt;
+};
+static_assert(sizeof(BSys) % 8 == 0, "BSys is copied as 64-bit words");
+struct BItem { int sys, eblk, o0, o1; };   // apply: E elements of block eblk, orbitals [o0, o1)
+struct BRow { int sys, o, rblk, pad; };    // one row block of one orbital
+struct BOrb { int sys, o; };               // one orbital of one system
+
+// elements.cu
+size_t hbar_batch_smem(int P1, int prec, int E);
+cudaError_t hbar_batch_occupancy(int P1, int prec, int E, int* blocks_per_sm);
+cudaError_t launch_hbar_batch(int P1, int prec, const BSys* sys, const BItem* items, int n_items,
+                              int E, int grid, const void* tab, cudaStream_t st);
+cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st);
+cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_rows,
+                             cudaStream_t st);
+// krylov.cu
+cudaError_t launch_bkry_init(const BSys* sys, const BOrb* orbs, int n_orbs, double factor,
+                             cudaStream_t st);
+cudaError_t launch_bkry_prepare(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
+                                int n_rows, cudaStream_t st);
+cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n_orbs, double tol,
+                            cudaStream_t st);
+cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
+                               int n_rows, cudaStream_t st);
+cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, cudaStream_t st);
+cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs,
+                                 int n_orbs, int* iter, int cap, int* err, cudaStream_t st);
+cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
+                              unsigned long long* dof_applies, int* kseen, cudaStream_t st);
+// capturable forms of the per-system field work (no host synchronization)
+tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err);
+tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err);
+tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter,
+                       int* err);
+tdks_status dipole_graph(tdks_ctx* c, const double* rho, double* base, const int* step,
+                         int64_t step_stride);
+cudaError_t launch_counter_add(int* counter, int inc, cudaStream_t st);

@@ -53,6 +53,11 @@ class TDKSError(RuntimeError):
     pass
 
 
+class TileChoice(C.Structure):
+    _fields_ = [("p", C.c_int), ("n_orb", C.c_int), ("elems_per_cta", C.c_int),
+                ("orbs_per_item", C.c_int), ("ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -90,11 +95,25 @@ def lib():
         "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
         "tdks_objective_forward": [v, p, i, i, d, _dp, _dp, _dp, i, d, i, i, _dp, _dp],
         "tdks_objective_backward": [v, i, _dp],
+        "tdks_batch_create": [i, p, p, _dp, i, d, i, C.POINTER(C.c_void_p)],
+        "tdks_batch_destroy": [v],
+        "tdks_batch_stream": [v],
+        "tdks_batch_sizes": [v, i, C.POINTER(i64), C.POINTER(i64), C.POINTER(i), C.POINTER(i)],
+        "tdks_batch_set_orbitals": [v, i, p],
+        "tdks_batch_get_orbitals": [v, i, p],
+        "tdks_batch_kick": [v, _dp, _dp],
+        "tdks_batch_init": [v, _dp],
+        "tdks_batch_tune": [v, i, p, i, C.POINTER(i)],
+        "tdks_batch_steps": [v, i, _dp],
+        "tdks_batch_stats": [v, C.POINTER(i64), C.POINTER(i), i],
+        "tdks_batch_last_error": [v],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name in ("tdks_last_error", "tdks_status_string") else C.c_int
+        f.restype = (C.c_char_p if name in ("tdks_last_error", "tdks_status_string",
+                                             "tdks_batch_last_error")
+                     else C.c_void_p if name == "tdks_batch_stream" else C.c_int)
     _lib = L
     return L
 
@@ -106,7 +125,11 @@ def exported_symbols() -> list:
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
-                        "tdks_objective_backward", "tdks_last_error", "tdks_status_string")]
+                        "tdks_objective_backward", "tdks_batch_create", "tdks_batch_destroy",
+                        "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
+                        "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
+                        "tdks_batch_tune", "tdks_batch_steps", "tdks_batch_stats",
+                        "tdks_batch_last_error", "tdks_last_error", "tdks_status_string")]
 
 
 def _darr(a) -> np.ndarray:
@@ -367,3 +390,118 @@ class DipoleObjective(torch.autograd.Function):
         g = fctx.tdctx.objective_backward(fctx.n_s)
         gE = torch.from_numpy(g).to(device=dev, dtype=dt_).reshape(shape) * gJ
         return (gE,) + (None,) * 10
+
+
+def _descs(cfg, keep):
+    """tdks_mesh_desc / tdks_system_desc of a workload config (arrays kept alive in keep)."""
+    arrs = [_darr(cfg.X), _darr(cfg.Y), _darr(cfg.Z), _darr(cfg.occ)]
+    R = _darr(cfg.atom_R if cfg.atom_R is not None else np.zeros((0, 3))).reshape(-1)
+    Zc = _darr(cfg.atom_Z if cfg.atom_Z is not None else np.zeros(0))
+    keep += arrs + [R, Zc]
+    m = MeshDesc(len(cfg.X) - 1, len(cfg.Y) - 1, len(cfg.Z) - 1, _ptr(arrs[0]), _ptr(arrs[1]),
+                 _ptr(arrs[2]), int(cfg.p), int(cfg.nq))
+    s = SystemDesc(int(cfg.n_orb), _ptr(arrs[3]), len(Zc), _ptr(R) if len(Zc) else None,
+                   _ptr(Zc) if len(Zc) else None, NUC_KIND[cfg.nuc_kind], float(cfg.nuc_param),
+                   int(bool(cfg.hartree)), int(bool(cfg.xc)))
+    return m, s
+
+
+class Batch:
+    """Owns a tdks_batch: many independent systems advanced together, one CUDA graph
+    per step (tdks_batch_* entry points).  All work runs on the batch's own stream."""
+
+    def __init__(self, cfgs, dts, prec: int = FP64, tol: float = 1e-10, k_max: int = 64):
+        L = lib()
+        keep = []
+        ms, ss = [], []
+        for cfg in cfgs:
+            m, s = _descs(cfg, keep)
+            ms.append(m)
+            ss.append(s)
+        n = len(cfgs)
+        M = (MeshDesc * n)(*ms)
+        S = (SystemDesc * n)(*ss)
+        dt = _darr(dts)
+        h = C.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        st = L.tdks_batch_create(n, C.cast(M, C.c_void_p), C.cast(S, C.c_void_p), _ptr(dt), prec,
+                                 tol, k_max, C.byref(h))
+        if st != 0:
+            raise TDKSError(f"tdks_batch_create: {L.tdks_status_string(st).decode()}: "
+                            f"{L.tdks_batch_last_error(None).decode()}")
+        self.h = h
+        self.n_sys = n
+        self.prec = prec
+        self.sizes = []
+        for k in range(n):
+            ni, ne, nq3, no = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+            L.tdks_batch_sizes(h, k, C.byref(ni), C.byref(ne), C.byref(nq3), C.byref(no))
+            self.sizes.append({"n_int": ni.value, "n_elem": ne.value, "nq3": nq3.value,
+                               "n_orb": no.value})
+
+    def _check(self, st: int, name: str):
+        if st != 0:
+            L = lib()
+            raise TDKSError(f"{name}: {L.tdks_status_string(st).decode()}: "
+                            f"{L.tdks_batch_last_error(self.h).decode()}")
+
+    @property
+    def stream(self) -> int:
+        return int(lib().tdks_batch_stream(self.h) or 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tdks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_orbitals(self, k: int, psi: torch.Tensor):
+        z = self.sizes[k]
+        if tuple(psi.shape) != (z["n_orb"], z["n_int"]):
+            raise TDKSError(f"set_orbitals: expected shape {(z['n_orb'], z['n_int'])}")
+        torch.cuda.current_stream().synchronize()
+        self._check(lib().tdks_batch_set_orbitals(self.h, k, _dev(psi, torch.complex128, "psi")),
+                    "tdks_batch_set_orbitals")
+
+    def get_orbitals(self, k: int) -> torch.Tensor:
+        z = self.sizes[k]
+        out = torch.empty((z["n_orb"], z["n_int"]), dtype=torch.complex128, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        self._check(lib().tdks_batch_get_orbitals(self.h, k, out.data_ptr()), "tdks_batch_get_orbitals")
+        return out
+
+    def kick(self, kappa, directions):
+        ka = _darr(kappa).reshape(self.n_sys)
+        di = _darr(directions).reshape(self.n_sys, 3)
+        self._check(lib().tdks_batch_kick(self.h, _ptr(ka), _ptr(di)), "tdks_batch_kick")
+
+    def init(self) -> np.ndarray:
+        d = np.zeros((self.n_sys, 3))
+        self._check(lib().tdks_batch_init(self.h, _ptr(d)), "tdks_batch_init")
+        return d
+
+    def tune(self, reps: int = 3) -> list:
+        cap = 64
+        out = (TileChoice * cap)()
+        n = C.c_int()
+        self._check(lib().tdks_batch_tune(self.h, reps, C.cast(out, C.c_void_p), cap, C.byref(n)),
+                    "tdks_batch_tune")
+        return [{"p": t.p, "n_orb": t.n_orb, "elems_per_cta": t.elems_per_cta,
+                 "orbs_per_item": t.orbs_per_item, "ms": t.ms} for t in out[:n.value]]
+
+    def steps(self, n_steps: int) -> np.ndarray:
+        """n_steps steps of every system; dipoles [n_steps, n_sys, 3]."""
+        d = np.zeros((max(n_steps, 1), self.n_sys, 3))
+        self._check(lib().tdks_batch_steps(self.h, n_steps, _ptr(d)), "tdks_batch_steps")
+        return d[:n_steps]
+
+    def stats(self, reset: bool = False) -> dict:
+        dof, k = C.c_int64(), C.c_int()
+        self._check(lib().tdks_batch_stats(self.h, C.byref(dof), C.byref(k), int(reset)),
+                    "tdks_batch_stats")
+        return {"dof_applies": dof.value, "k_max_seen": k.value}

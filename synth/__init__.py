@@ -212,6 +212,53 @@ def pulse_samples(params, pc: PulseConfig):
     return (e[..., None] * d).reshape(pc.n_steps, 6)
 
 
+BATCH_SEED = 18101305
+
+
+def config5(n_sys: int = 64, seed: int = BATCH_SEED):
+    """Batch of independent systems of uneven size: n^3 elements (n in 4..12, 2 bohr
+    wide), p in 4..8, 1-8 doubly occupied orbitals, 1-4 soft-Coulomb nuclei (Z in
+    1..4) inside a third of the box, own kick direction, dt in {0.02, 0.05, 0.1}.
+    Returns (configs, dts, kick directions)."""
+    rng = np.random.default_rng(seed)
+    cfgs, dts, dirs = [], [], []
+    for k in range(n_sys):
+        n = int(rng.integers(4, 13))
+        p = int(rng.integers(4, 9))
+        n_orb = int(rng.integers(1, 9))
+        n_nuc = int(rng.integers(1, 5))
+        L = float(n)
+        b = uniform_breaks(-L, L, n)
+        R = rng.uniform(-L / 3, L / 3, size=(n_nuc, 3))
+        Z = rng.integers(1, 5, size=n_nuc).astype(float)
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        cfgs.append(SystemConfig(
+            name=f"batch{k}_{n}^3_p{p}_o{n_orb}", X=b, Y=b.copy(), Z=b.copy(), p=p, n_orb=n_orb,
+            occ=np.full(n_orb, 2.0), atom_R=R, atom_Z=Z, nuc_kind="soft", nuc_param=0.5,
+            kick=1e-3, kick_dir=tuple(d), dt=float(rng.choice([0.02, 0.05, 0.1])), n_steps=200,
+            tol=1e-10, k_max=64, seed=seed + k))
+        dts.append(cfgs[-1].dt)
+        dirs.append(d)
+    return cfgs, np.array(dts), np.array(dirs)
+
+
+def small_batch(seed: int = 11):
+    """A few small uneven systems (degrees 2-5, 1-3 orbitals, own time steps) for
+    parity tests of the batched path."""
+    rng = np.random.default_rng(seed)
+    specs = [((3, 2, 2), 3, 2, 0.05), ((2, 2, 2), 2, 1, 0.1), ((2, 3, 2), 4, 3, 0.02),
+             ((2, 2, 3), 5, 1, 0.05), ((3, 3, 2), 3, 2, 0.1)]
+    cfgs = []
+    for k, (n, p, no, dt) in enumerate(specs):
+        c = small_config(*n, p=p, n_orb=no, seed=seed + k)
+        c.dt = dt
+        d = rng.standard_normal(3)
+        c.kick_dir = tuple(d / np.linalg.norm(d))
+        cfgs.append(c)
+    return cfgs
+
+
 def small_config(nx=3, ny=2, nz=2, p=3, n_orb=2, L=6.0, seed=7, nuc_kind="soft",
                  hartree=True, xc=True, graded=False) -> SystemConfig:
     """A small test system with uneven element counts and (optionally) uneven sizes."""
