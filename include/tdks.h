@@ -254,7 +254,8 @@ tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
  *   orbitals (as tdks_init_propagation for every system).
  * tdks_batch_tune: chooses the elements per CTA of every degree and the orbitals
  *   per work item of every (degree, orbital count) class by timing `reps`
- *   launches of each candidate; writes up to cap choices (tile table) to out.
+ *   (1..32) launches of each candidate; writes up to cap choices (tile table)
+ *   to out.
  *   Optional; without it the largest tile and one orbital per item are used.
  * tdks_batch_steps: n_steps steps of every system; dipoles [n_steps][n_sys][3].
  *   Synchronizes.  TDKS_ERR_NOT_CONVERGED if a Lanczos loop failed or hit its
@@ -283,6 +284,18 @@ tdks_status tdks_batch_init(tdks_batch* b, double* dip_host);
 tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out);
 tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host);
 tdks_status tdks_batch_stats(tdks_batch* b, int64_t* dof_applies, int* k_max_seen, int reset);
+/* Phase timing of the step graph (diagnostics): with timing on, the graph records
+ * CUDA events at the phase boundaries; tdks_batch_phase_ms gives the device time
+ * of the last step's phases [predictor, half-step exponential, corrector
+ * fields, full-step exponential, history + dipole] and the loop passes of the two
+ * exponentials.  Turning timing on or off rebuilds the graph. */
+tdks_status tdks_batch_set_timing(tdks_batch* b, int on);
+tdks_status tdks_batch_phase_ms(tdks_batch* b, double ms[5], int passes[2]);
+/* The half-step exponential of the current state once more, outside the graph,
+ * kernel group by kernel group (as many passes as the last step's half-step
+ * loop): ms = device time of [norms, apply, alpha, assembly, small exponentials,
+ * recombination].  Overwrites only internal scratch; the state is unchanged. */
+tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]);
 const char* tdks_batch_last_error(const tdks_batch* b);
 
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar

@@ -32,8 +32,10 @@
 
 namespace {
 
-constexpr int kMaxSubPasses = 16;
-std::string g_create_err;           // message of the last failed tdks_batch_create   // loop cap = kMaxSubPasses * k_max passes
+constexpr int kMaxSubPasses = 16;   // loop cap = kMaxSubPasses * k_max passes
+constexpr int kFieldStreams = 16;   // parallel branches of the per-system field work
+constexpr int kDegStreams = 9;      // parallel branches of the per-degree applies
+std::string g_create_err;           // message of the last failed tdks_batch_create
 
 struct Deg {
   int P1 = 0, E = 1, grid = 1, n_items = 0;
@@ -47,6 +49,11 @@ struct tdks_batch {
   int n_sys = 0, prec = 0, kmax = 64, cg_iters = 4, n_sm = 152;
   double tol = 1e-10;
   cudaStream_t st = nullptr, st_body = nullptr;
+  cudaStream_t fs[kFieldStreams] = {};   // capture-only fork streams (field work)
+  cudaStream_t ds[kDegStreams] = {};     // capture-only fork streams (loop body)
+  cudaEvent_t fork_ev = nullptr, body_fork_ev = nullptr;
+  cudaEvent_t join_ev[kFieldStreams] = {}, body_join_ev[kDegStreams] = {};
+  std::vector<int> field_order;          // systems by decreasing size
   std::vector<tdks_ctx*> ctx;
   std::vector<int> n_orb, n_eblk, n_rblk, opb;
   std::vector<double> dt;
@@ -62,12 +69,15 @@ struct tdks_batch {
   int n_rows = 0;
   std::vector<Deg> degs;
   int* d_ctrl = nullptr;            // [0], [1]: pass counters, [2]: error bits, [3]: step, [4]: k seen
+  int* d_qctr = nullptr;            // work ticket counters of the apply launches (one per degree)
   unsigned long long* d_dof = nullptr;
   double* d_dip = nullptr;
   int dip_cap = 256;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool orbitals_set = false, ready = false;
+  bool timing = false;              // event nodes at the phase boundaries of the step graph
+  cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<tdks_tile_choice> tiles;
   std::string err;
 };
@@ -119,9 +129,22 @@ void free_batch(tdks_batch* b) {
   for (auto* p : b->apart) cudaFree(p);
   for (auto* p : b->npart) cudaFree(p);
   for (auto& d : b->degs) cudaFree(d.d_items);
-  void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_dof, b->d_dip};
+  void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_qctr,
+                  b->d_dof, b->d_dip};
   for (void* p : ptrs) cudaFree(p);
   for (auto* c : b->ctx) tdks_destroy(c);
+  for (auto& e : b->tev)
+    if (e) cudaEventDestroy(e);
+  for (auto& x : b->fs)
+    if (x) cudaStreamDestroy(x);
+  for (auto& x : b->ds)
+    if (x) cudaStreamDestroy(x);
+  for (auto& e : b->join_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : b->body_join_ev)
+    if (e) cudaEventDestroy(e);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->body_fork_ev) cudaEventDestroy(b->body_fork_ev);
   if (b->st_body) cudaStreamDestroy(b->st_body);
   if (b->st) cudaStreamDestroy(b->st);
   delete b;
@@ -195,14 +218,24 @@ tdks_status build_degree(tdks_batch* b, Deg& d, int E) {
 tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphConditionalHandle h) {
   cudaStream_t s = b->st_body;
   B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
-  for (const Deg& d : b->degs)
-    B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, s));
+  // the degree classes touch disjoint systems: concurrent branches, so that the
+  // tail of one persistent grid overlaps the next
+  const int nd = (int)b->degs.size();
+  B_CU(b, cudaEventRecord(b->body_fork_ev, s));
+  for (int i = 0; i < nd; ++i) {
+    const Deg& d = b->degs[i];
+    B_CU(b, cudaStreamWaitEvent(b->ds[i], b->body_fork_ev, 0));
+    B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, b->d_qctr + i,
+                              b->ds[i]));
+    B_CU(b, cudaEventRecord(b->body_join_ev[i], b->ds[i]));
+  }
+  for (int i = 0; i < nd; ++i) B_CU(b, cudaStreamWaitEvent(s, b->body_join_ev[i], 0));
   B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
   B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
   B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, s));
   B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
   B_CU(b, launch_bloop_control(h, sys, b->d_orbs, b->n_gorb, iter, kMaxSubPasses * b->kmax,
-                               b->d_ctrl + 2, s));
+                               b->d_ctrl + 2, b->d_qctr, kDegStreams, s));
   return TDKS_OK;
 }
 
@@ -232,20 +265,44 @@ tdks_status add_loop(tdks_batch* b, const BSys* sys, int* iter, cudaGraphConditi
   return TDKS_OK;
 }
 
+// Per-system field work on parallel capture branches: system field_order[k] runs on
+// fork stream k % kFieldStreams (its context's stream is pointed there); the join
+// returns every context to the batch stream.
+tdks_status fork_fields(tdks_batch* b) {
+  B_CU(b, cudaEventRecord(b->fork_ev, b->st));
+  for (int i = 0; i < kFieldStreams; ++i) B_CU(b, cudaStreamWaitEvent(b->fs[i], b->fork_ev, 0));
+  for (int k = 0; k < b->n_sys; ++k) b->ctx[b->field_order[k]]->stream = b->fs[k % kFieldStreams];
+  return TDKS_OK;
+}
+
+tdks_status join_fields(tdks_batch* b) {
+  for (int i = 0; i < kFieldStreams; ++i) {
+    B_CU(b, cudaEventRecord(b->join_ev[i], b->fs[i]));
+    B_CU(b, cudaStreamWaitEvent(b->st, b->join_ev[i], 0));
+  }
+  for (auto* c : b->ctx) c->stream = b->st;
+  return TDKS_OK;
+}
+
 tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2) {
   const double zero[3] = {0.0, 0.0, 0.0};
   int* err = b->d_ctrl + 2;
+  auto mark = [&](int i) -> cudaError_t { return b->timing ? cudaEventRecordWithFlags(b->tev[i], b->st, cudaEventRecordExternal) : cudaSuccess; };
+  B_CU(b, mark(0));
   // predictor potential V_N + 1.25 V_HXC^{n-1} - 0.25 V_HXC^{n-2} (no external field)
   for (int s = 0; s < b->n_sys; ++s) {
     tdks_ctx* c = b->ctx[s];
     B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.25, c->d_vhxc1, -0.25, c->d_vhxc2,
                                           nullptr, zero)), "predictor");
   }
+  B_CU(b, mark(1));
   B_CU(b, launch_bkry_init(b->d_half, b->d_orbs, b->n_gorb, 0.5, b->st));
-  B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->st));
+  B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->d_qctr, kDegStreams, b->st));
   B_TRY(b, add_loop(b, b->d_half, b->d_ctrl + 0, h1), "half step");
   B_CU(b, launch_bkry_stats(b->d_half, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  B_CU(b, mark(2));
   // corrector potential from the density of psi^{n-1/2}
+  B_TRY(b, fork_fields(b), "fork");
   for (int s = 0; s < b->n_sys; ++s) {
     tdks_ctx* c = b->ctx[s];
     B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err)),
@@ -253,20 +310,26 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
     B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr,
                                           zero)), "corrector");
   }
+  B_TRY(b, join_fields(b), "join");
+  B_CU(b, mark(3));
   B_CU(b, launch_bkry_init(b->d_full, b->d_orbs, b->n_gorb, 1.0, b->st));
-  B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->st));
+  B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->d_qctr, kDegStreams, b->st));
   B_TRY(b, add_loop(b, b->d_full, b->d_ctrl + 1, h2), "full step");
   B_CU(b, launch_bkry_stats(b->d_full, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  B_CU(b, mark(4));
   // history and dipole of every system
+  B_TRY(b, fork_fields(b), "fork");
   for (int s = 0; s < b->n_sys; ++s) {
     tdks_ctx* c = b->ctx[s];
     const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
-    B_CU(b, cudaMemcpyAsync(c->d_vhxc2, c->d_vhxc1, fb, cudaMemcpyDeviceToDevice, b->st));
+    B_CU(b, cudaMemcpyAsync(c->d_vhxc2, c->d_vhxc1, fb, cudaMemcpyDeviceToDevice, c->stream));
     B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err)), "history");
     B_TRY(b, ctx_try(b, c, dipole_graph(c, c->d_rho, b->d_dip + 3 * (size_t)s, b->d_ctrl + 3,
                                         3 * (int64_t)b->n_sys)), "dipole");
   }
+  B_TRY(b, join_fields(b), "join");
   B_CU(b, launch_counter_add(b->d_ctrl + 3, 1, b->st));
+  B_CU(b, mark(5));
   return TDKS_OK;
 }
 
@@ -279,6 +342,7 @@ tdks_status build_graph(tdks_batch* b) {
   B_CU(b, cudaGraphConditionalHandleCreate(&h2, b->graph, 0, cudaGraphCondAssignDefault));
   B_CU(b, cudaStreamBeginCaptureToGraph(b->st, b->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   tdks_status s = capture_step(b, h1, h2);
+  for (auto* c : b->ctx) c->stream = b->st;
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->st, &out);
   if (s != TDKS_OK) {
@@ -305,10 +369,12 @@ tdks_status time_apply(tdks_batch* b, const Deg& d, const std::vector<BItem>& it
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaError_t ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, b->st);
+  int* q = b->d_qctr;
+  cudaMemsetAsync(q, 0, sizeof(int) * (reps + 1), b->st);
+  cudaError_t ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, q, b->st);
   cudaEventRecord(e0, b->st);
   for (int r = 0; r < reps && ce == cudaSuccess; ++r)
-    ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, b->st);
+    ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, q + 1 + r, b->st);
   cudaEventRecord(e1, b->st);
   cudaError_t se = cudaEventSynchronize(e1);
   float t = 0.f;
@@ -350,6 +416,26 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
       cudaStreamCreateWithFlags(&b->st_body, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     b->err = "stream creation";
+    return fail(TDKS_ERR_CUDA);
+  }
+  for (int i = 0; i < kFieldStreams; ++i)
+    if (cudaStreamCreateWithFlags(&b->fs[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      b->err = "stream creation";
+      return fail(TDKS_ERR_CUDA);
+    }
+  for (int i = 0; i < kDegStreams; ++i)
+    if (cudaStreamCreateWithFlags(&b->ds[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->body_join_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      b->err = "stream creation";
+      return fail(TDKS_ERR_CUDA);
+    }
+  if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->body_fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "event creation";
     return fail(TDKS_ERR_CUDA);
   }
   int dev = 0;
@@ -438,11 +524,16 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
       b->degs.push_back(d);
     }
   }
+  b->field_order.resize(n_sys);
+  for (int s = 0; s < n_sys; ++s) b->field_order[s] = s;
+  std::stable_sort(b->field_order.begin(), b->field_order.end(), [&](int x, int y) {
+    return b->ctx[x]->n_int * b->n_orb[x] > b->ctx[y]->n_int * b->n_orb[y];
+  });
   b->n_gorb = (int)orbs.size();
   b->n_rows = (int)rows.size();
   if (balloc(b, &b->d_half, n_sys) || balloc(b, &b->d_full, n_sys) || balloc(b, &b->d_orbs, orbs.size()) ||
       balloc(b, &b->d_rows, rows.size()) || balloc(b, &b->d_rows_asm, rows.size()) ||
-      balloc(b, &b->d_ctrl, 8) || balloc(b, &b->d_dof, 1) ||
+      balloc(b, &b->d_ctrl, 8) || balloc(b, &b->d_qctr, 64) || balloc(b, &b->d_dof, 1) ||
       balloc(b, &b->d_dip, (size_t)b->dip_cap * n_sys * 3))
     return fail(TDKS_ERR_NOMEM);
   // assembly items: larger systems first, so their many row blocks start early
@@ -454,6 +545,7 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(BRow), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_rows_asm, rows_asm.data(), rows_asm.size() * sizeof(BRow), cudaMemcpyHostToDevice);
   cudaMemset(b->d_ctrl, 0, 8 * sizeof(int));
+  cudaMemset(b->d_qctr, 0, 64 * sizeof(int));
   cudaMemset(b->d_dof, 0, sizeof(unsigned long long));
   for (Deg& d : b->degs)
     if (build_degree(b, d, emax_of(d.P1)) != TDKS_OK) return fail(TDKS_ERR_CUDA);
@@ -529,7 +621,7 @@ tdks_status tdks_batch_init(tdks_batch* b, double* dip_host) {
 }
 
 tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out) {
-  if (!b || reps < 1) return TDKS_ERR_ARG;
+  if (!b || reps < 1 || reps > 32) return TDKS_ERR_ARG;
   if (!b->orbitals_set) return bfail(b, TDKS_ERR_ARG, "tune after tdks_batch_init (needs the orbitals)");
   invalidate_graph(b);
   // every orbital active at j = 0: the apply reads the orbitals themselves
@@ -625,6 +717,73 @@ tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host) {
     if (dip_host) std::memcpy(dip_host + (size_t)done * b->n_sys * 3, buf.data(), buf.size() * sizeof(double));
     done += chunk;
   }
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_set_timing(tdks_batch* b, int on) {
+  if (!b) return TDKS_ERR_ARG;
+  if ((bool)on == b->timing) return TDKS_OK;
+  for (auto& e : b->tev)
+    if (!e) B_CU(b, cudaEventCreate(&e));
+  b->timing = on != 0;
+  invalidate_graph(b);
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_phase_ms(tdks_batch* b, double ms[5], int passes[2]) {
+  if (!b || !ms) return TDKS_ERR_ARG;
+  if (!b->timing || !b->exec) return bfail(b, TDKS_ERR_ARG, "enable timing and run a step first");
+  B_CU(b, cudaStreamSynchronize(b->st));
+  for (int i = 0; i < 5; ++i) {
+    float t = 0.f;
+    B_CU(b, cudaEventElapsedTime(&t, b->tev[i], b->tev[i + 1]));
+    ms[i] = t;
+  }
+  if (passes) B_CU(b, cudaMemcpy(passes, b->d_ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  return TDKS_OK;
+}
+
+// Diagnostics: the half-step exponential of the current state run once more outside
+// the graph, kernel group by kernel group, with the pass count of the last step's
+// half-step loop; ms = device time of [norms/start, apply, alpha, assembly,
+// small exponentials, recombination].  Writes only the scratch output psi_half.
+tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]) {
+  if (!b || !ms) return TDKS_ERR_ARG;
+  int ctrl[8];
+  B_CU(b, cudaMemcpy(ctrl, b->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+  const int passes = ctrl[0];
+  if (passes < 1) return bfail(b, TDKS_ERR_ARG, "run a step first");
+  cudaEvent_t ev[7];
+  for (auto& e : ev) B_CU(b, cudaEventCreate(&e));
+  for (int i = 0; i < 6; ++i) ms[i] = 0.0;
+  const BSys* sys = b->d_half;
+  B_CU(b, launch_bkry_init(sys, b->d_orbs, b->n_gorb, 0.5, b->st));
+  for (int it = 0; it < passes; ++it) {
+    B_CU(b, cudaMemsetAsync(b->d_qctr, 0, 64 * sizeof(int), b->st));
+    B_CU(b, cudaEventRecord(ev[0], b->st));
+    B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
+    B_CU(b, cudaEventRecord(ev[1], b->st));
+    for (size_t i = 0; i < b->degs.size(); ++i) {
+      const Deg& d = b->degs[i];
+      B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, b->d_qctr + i, b->st));
+    }
+    B_CU(b, cudaEventRecord(ev[2], b->st));
+    B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, b->st));
+    B_CU(b, cudaEventRecord(ev[3], b->st));
+    B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, b->st));
+    B_CU(b, cudaEventRecord(ev[4], b->st));
+    B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->st));
+    B_CU(b, cudaEventRecord(ev[5], b->st));
+    B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
+    B_CU(b, cudaEventRecord(ev[6], b->st));
+    B_CU(b, cudaEventSynchronize(ev[6]));
+    for (int i = 0; i < 6; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
   return TDKS_OK;
 }
 

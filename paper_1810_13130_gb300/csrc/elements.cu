@@ -280,8 +280,15 @@ __device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<
   constexpr bool kF32 = std::is_same<T, float>::value;
   constexpr bool kDF = std::is_same<T, Df>::value;
   const int rows = g.niy * g.niz;
+  // short rows (fewer nodes than threads) are processed several at a time
+  const int nix = g.nix, nt = (int)blockDim.x;
+  const int rpb = nix >= nt ? 1 : nt / nix;                 // rows in flight per block
+  const int tr = nix >= nt ? 0 : (int)threadIdx.x / nix;    // this thread's row slot
+  const int tI = nix >= nt ? (int)threadIdx.x : (int)threadIdx.x % nix;
+  const int tstep = nix >= nt ? nt : nix;
   double acc = 0.0;
-  for (int r = r0; r < rows; r += rstride) {
+  if (tr >= rpb) return acc;
+  for (int r = r0 + tr * rstride; r < rows; r += rpb * rstride) {
     const int J = r % g.niy + 1, K = r / g.niy + 1;
     int ey[2], by[2], ez[2], bz[2], ex[2], bx[2];
     const int ny = node_elems(J, g.p, g.ny, ey, by);
@@ -289,7 +296,7 @@ __device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<
     const double syz = g.s[1][J] * g.s[2][K];
     const float syzf = g.sf[1][J] * g.sf[2][K];
     const long long rowbase = (long long)g.nix * (r);
-    for (int I = threadIdx.x + 1; I <= g.nix; I += blockDim.x) {
+    for (int I = tI + 1; I <= g.nix; I += tstep) {
       const int nx = node_elems(I, g.p, g.nx, ex, bx);
       double re = 0.0, im = 0.0;
       float fre = 0.f, fim = 0.f;
@@ -387,7 +394,7 @@ __device__ __forceinline__ const double2* bvec(const BSys& S, const KryOrb& K, i
 template <int P1, typename T>
 __global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ sys,
                                                     const BItem* __restrict__ items, int n_items,
-                                                    const T* __restrict__ tab) {
+                                                    const T* __restrict__ tab, int* __restrict__ qctr) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   typedef Cx<T> V;
@@ -407,12 +414,21 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ 
   __syncthreads();
   // the current item's system descriptor is staged in shared memory: its fields are
   // re-read where used instead of occupying registers across the element body
+  // items are taken from a shared ticket counter (zeroed before every launch), so
+  // CTAs that draw items of finished orbitals move on at once and the grid stays
+  // balanced whatever the mix of active orbitals
   __shared__ BSys sS;
   __shared__ BItem sW;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  __shared__ int sIt;
+  for (;;) {
     __syncthreads();
-    if (tid == 0) sW = items[it];
+    if (tid == 0) {
+      const int it = atomicAdd(qctr, 1);
+      sIt = it;
+      if (it < n_items) sW = items[it];
+    }
     __syncthreads();
+    if (sIt >= n_items) break;
     for (int i = tid; i < (int)(sizeof(BSys) / 8); i += nthr)
       reinterpret_cast<long long*>(&sS)[i] = reinterpret_cast<const long long*>(&sys[sW.sys])[i];
     __syncthreads();
@@ -1178,7 +1194,7 @@ size_t hbar_batch_smem(int P1, int prec, int E) {
 
 template <int P1, typename T>
 static cudaError_t hbar_batch_launch_t(const BSys* sys, const BItem* items, int n_items, int E,
-                                       int grid, const void* tab, cudaStream_t st, int* occ) {
+                                       int grid, const void* tab, int* qctr, cudaStream_t st, int* occ) {
   const size_t smem = hbar_batch_smem_t<P1, T>(E);
   // the kernel also holds ~330 B of static shared memory: opt in for any large size
   cudaError_t e = cudaFuncSetAttribute(k_hbar_batch<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1187,43 +1203,43 @@ static cudaError_t hbar_batch_launch_t(const BSys* sys, const BItem* items, int 
   if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_hbar_batch<P1, T>, Cfg<P1>::P2 * E, smem);
   if (n_items <= 0) return cudaSuccess;
   k_hbar_batch<P1, T><<<grid, dim3(Cfg<P1>::P2, E), smem, st>>>(sys, items, n_items,
-                                                               static_cast<const T*>(tab));
+                                                               static_cast<const T*>(tab), qctr);
   return cudaGetLastError();
 }
 
 template <int P1>
 static cudaError_t hbar_batch_p(int prec, const BSys* sys, const BItem* items, int n_items, int E,
-                                int grid, const void* tab, cudaStream_t st, int* occ) {
+                                int grid, const void* tab, int* qctr, cudaStream_t st, int* occ) {
   if (E < 1 || Cfg<P1>::P2 * E > 256) return cudaErrorInvalidValue;
-  if (prec == TDKS_FP32) return hbar_batch_launch_t<P1, float>(sys, items, n_items, E, grid, tab, st, occ);
-  if (prec == TDKS_DF64) return hbar_batch_launch_t<P1, Df>(sys, items, n_items, E, grid, tab, st, occ);
-  return hbar_batch_launch_t<P1, double>(sys, items, n_items, E, grid, tab, st, occ);
+  if (prec == TDKS_FP32) return hbar_batch_launch_t<P1, float>(sys, items, n_items, E, grid, tab, qctr, st, occ);
+  if (prec == TDKS_DF64) return hbar_batch_launch_t<P1, Df>(sys, items, n_items, E, grid, tab, qctr, st, occ);
+  return hbar_batch_launch_t<P1, double>(sys, items, n_items, E, grid, tab, qctr, st, occ);
 }
 
 static cudaError_t hbar_batch_dispatch(int P1, int prec, const BSys* sys, const BItem* items,
-                                       int n_items, int E, int grid, const void* tab,
+                                       int n_items, int E, int grid, const void* tab, int* qctr,
                                        cudaStream_t st, int* occ) {
   switch (P1) {
-    case 2: return hbar_batch_p<2>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 3: return hbar_batch_p<3>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 4: return hbar_batch_p<4>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 5: return hbar_batch_p<5>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 6: return hbar_batch_p<6>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 7: return hbar_batch_p<7>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 8: return hbar_batch_p<8>(prec, sys, items, n_items, E, grid, tab, st, occ);
-    case 9: return hbar_batch_p<9>(prec, sys, items, n_items, E, grid, tab, st, occ);
+    case 2: return hbar_batch_p<2>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 3: return hbar_batch_p<3>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 4: return hbar_batch_p<4>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 5: return hbar_batch_p<5>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 6: return hbar_batch_p<6>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 7: return hbar_batch_p<7>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 8: return hbar_batch_p<8>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
+    case 9: return hbar_batch_p<9>(prec, sys, items, n_items, E, grid, tab, qctr, st, occ);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t hbar_batch_occupancy(int P1, int prec, int E, int* blocks_per_sm) {
   *blocks_per_sm = 0;
-  return hbar_batch_dispatch(P1, prec, nullptr, nullptr, 0, E, 0, nullptr, nullptr, blocks_per_sm);
+  return hbar_batch_dispatch(P1, prec, nullptr, nullptr, 0, E, 0, nullptr, nullptr, nullptr, blocks_per_sm);
 }
 
 cudaError_t launch_hbar_batch(int P1, int prec, const BSys* sys, const BItem* items, int n_items,
-                              int E, int grid, const void* tab, cudaStream_t st) {
-  return hbar_batch_dispatch(P1, prec, sys, items, n_items, E, grid, tab, st, nullptr);
+                              int E, int grid, const void* tab, int* qctr, cudaStream_t st) {
+  return hbar_batch_dispatch(P1, prec, sys, items, n_items, E, grid, tab, qctr, st, nullptr);
 }
 
 cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st) {

@@ -507,7 +507,8 @@ __global__ void k_bkry_after(const BSys* __restrict__ sys, const BOrb* __restric
   }
 }
 
-__global__ void k_bloop_begin(cudaGraphConditionalHandle h, int* iter) {
+__global__ void k_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qctr, int n_q) {
+  if (threadIdx.x < n_q) qctr[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     *iter = 0;
     cudaGraphSetConditional(h, 1u);
@@ -517,8 +518,10 @@ __global__ void k_bloop_begin(cudaGraphConditionalHandle h, int* iter) {
 // Loop condition: continue while some orbital is still in the recurrence, none
 // failed and the pass count is below the cap (bit 1 of *err: failure, bit 2: cap).
 __global__ void k_bloop_control(cudaGraphConditionalHandle h, const BSys* __restrict__ sys,
-                                const BOrb* __restrict__ orbs, int n, int* iter, int cap, int* err) {
+                                const BOrb* __restrict__ orbs, int n, int* iter, int cap, int* err,
+                                int* qctr, int n_q) {
   __shared__ int s_act, s_fail;
+  if (threadIdx.x < n_q) qctr[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     s_act = 0;
     s_fail = 0;
@@ -725,14 +728,17 @@ cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n, const B
   return cudaGetLastError();
 }
 
-cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, cudaStream_t st) {
-  k_bloop_begin<<<1, 32, 0, st>>>(h, iter);
+cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qctr, int n_q,
+                               cudaStream_t st) {
+  if (n_q > 32) return cudaErrorInvalidValue;
+  k_bloop_begin<<<1, 32, 0, st>>>(h, iter, qctr, n_q);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs, int n,
-                                 int* iter, int cap, int* err, cudaStream_t st) {
-  k_bloop_control<<<1, kThreads, 0, st>>>(h, sys, orbs, n, iter, cap, err);
+                                 int* iter, int cap, int* err, int* qctr, int n_q, cudaStream_t st) {
+  if (n_q > kThreads) return cudaErrorInvalidValue;
+  k_bloop_control<<<1, kThreads, 0, st>>>(h, sys, orbs, n, iter, cap, err, qctr, n_q);
   return cudaGetLastError();
 }
 

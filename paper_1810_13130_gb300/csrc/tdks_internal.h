@@ -278,8 +278,9 @@ struct BOrb { int sys, o; };               // one orbital of one system
 // elements.cu
 size_t hbar_batch_smem(int P1, int prec, int E);
 cudaError_t hbar_batch_occupancy(int P1, int prec, int E, int* blocks_per_sm);
+// qctr: the launch's work ticket counter, zero at launch
 cudaError_t launch_hbar_batch(int P1, int prec, const BSys* sys, const BItem* items, int n_items,
-                              int E, int grid, const void* tab, cudaStream_t st);
+                              int E, int grid, const void* tab, int* qctr, cudaStream_t st);
 cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st);
 cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_rows,
                              cudaStream_t st);
@@ -292,9 +293,12 @@ cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n_orbs, doubl
                             cudaStream_t st);
 cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
                                int n_rows, cudaStream_t st);
-cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, cudaStream_t st);
+// the loop kernels also zero the n_q work ticket counters qctr for the next pass
+cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qctr, int n_q,
+                               cudaStream_t st);
 cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs,
-                                 int n_orbs, int* iter, int cap, int* err, cudaStream_t st);
+                                 int n_orbs, int* iter, int cap, int* err, int* qctr, int n_q,
+                                 cudaStream_t st);
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
                               unsigned long long* dof_applies, int* kseen, cudaStream_t st);
 // capturable forms of the per-system field work (no host synchronization)

@@ -107,6 +107,9 @@ def lib():
         "tdks_batch_steps": [v, i, _dp],
         "tdks_batch_stats": [v, C.POINTER(i64), C.POINTER(i), i],
         "tdks_batch_last_error": [v],
+        "tdks_batch_set_timing": [v, i],
+        "tdks_batch_phase_ms": [v, _dp, C.POINTER(i)],
+        "tdks_batch_profile_pass": [v, _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -129,7 +132,9 @@ def exported_symbols() -> list:
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
                         "tdks_batch_tune", "tdks_batch_steps", "tdks_batch_stats",
-                        "tdks_batch_last_error", "tdks_last_error", "tdks_status_string")]
+                        "tdks_batch_last_error", "tdks_batch_set_timing", "tdks_batch_phase_ms",
+                        "tdks_batch_profile_pass",
+                        "tdks_last_error", "tdks_status_string")]
 
 
 def _darr(a) -> np.ndarray:
@@ -499,6 +504,24 @@ class Batch:
         d = np.zeros((max(n_steps, 1), self.n_sys, 3))
         self._check(lib().tdks_batch_steps(self.h, n_steps, _ptr(d)), "tdks_batch_steps")
         return d[:n_steps]
+
+    def set_timing(self, on: bool):
+        self._check(lib().tdks_batch_set_timing(self.h, int(bool(on))), "tdks_batch_set_timing")
+
+    def phase_ms(self) -> dict:
+        """Device time of the last step's phases and the loop passes of its exponentials."""
+        ms = np.zeros(5)
+        passes = (C.c_int * 2)()
+        self._check(lib().tdks_batch_phase_ms(self.h, _ptr(ms), passes), "tdks_batch_phase_ms")
+        names = ("predictor", "half_exp", "corrector_fields", "full_exp", "history_dipole")
+        return {**dict(zip(names, ms.tolist())), "passes": list(passes)}
+
+    def profile_pass(self) -> dict:
+        """Kernel-group device times of the half-step exponential, re-run outside the graph."""
+        ms = np.zeros(6)
+        self._check(lib().tdks_batch_profile_pass(self.h, _ptr(ms)), "tdks_batch_profile_pass")
+        return dict(zip(("norms", "apply", "alpha", "assembly", "small_exp", "recombination"),
+                        ms.tolist()))
 
     def stats(self, reset: bool = False) -> dict:
         dof, k = C.c_int64(), C.c_int()
