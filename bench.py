@@ -33,7 +33,8 @@ METRIC = ("orbital-steps/s & HΨ GDoF/s, mixed/batched vs FP64 on 1 GB300 at dip
           "err≤1e-6")
 FP64_PEAK_TFLOPS = 1.25          # GB300 dense FP64 (profiling recipe table); probe: 1.256
 FP32_PEAK_TFLOPS = 73.5          # measured FFMA rate of this machine's GB300 (FMA probe)
-PROFILE = os.path.join(ROOT, "profiles", "hbar_fp64_molecule.txt")
+PROFILES = {"fp64": os.path.join(ROOT, "profiles", "hbar_fp64_molecule.txt"),
+            "df64": os.path.join(ROOT, "profiles", "hbar_df64_molecule.txt")}
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -197,19 +198,20 @@ class ClockSampler:
 def profile_traffic(prec: str):
     """dram bytes per Hbar launch from the committed ncu summary, if the kernel
     source has not changed since the capture."""
-    if prec != "fp64" or not os.path.exists(PROFILE):
+    path = PROFILES.get(prec)
+    if not path or not os.path.exists(path):
         return None
     src = open(os.path.join(ROOT, "paper_1810_13130_gb300", "csrc", "elements.cu"), "rb").read()
     h = hashlib.sha256(src).hexdigest()[:16]
     vals = {}
-    for line in open(PROFILE):
+    for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("elements_cu_sha256_16") != h:
         return None
     try:
-        return float(vals["dram_bytes_per_color_launch_full_size"])
+        return float(vals["dram_bytes_per_launch_full_size"])
     except (KeyError, ValueError):
         return None
 
