@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-system batched runs")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                    help="skip the adjoint-gradient timing on the pulse workload")
     ap.add_argument("--apply-only", action="store_true",
                     help="time standalone Hbar applications (16 orbitals) instead of steps")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -375,6 +377,8 @@ def ours(args, rank: int, world: int, local_rank: int):
         line["mixed"] = mixed
     if args.batched and args.prec == "fp64":
         line["batched"] = batched_section(tdks, torch, args, local_rank)
+    if args.adjoint and args.prec == "fp64":
+        line["adjoint"] = adjoint_section(tdks, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         recs = run_oracle_sample(1)
         st = [r for r in recs if "step" in r]
@@ -385,6 +389,51 @@ def ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def adjoint_section(tdks, torch) -> dict:
+    """Gradient of J = int d_z(t)^2 dt with respect to the 8 parameters of four
+    Gaussian pulses driving the atom workload (200 steps of dt 0.1, checkpoints every
+    20 steps): forward and adjoint device time, and the gradient against central
+    differences (h = 1e-5) of the same forward."""
+    import numpy as np
+    import synth
+    sc, pc = synth.config4()
+    gs = np.load(os.path.join(ROOT, "tests", "golden", "gs_atom_soft_Z2_6x6x6_p4.npz"))
+    ctx = tdks.Context.from_config(sc)
+    ctx.set_cg(1e-13)
+    psi0 = torch.from_numpy(gs["psibar"].astype(complex)).cuda()
+    w = pc.objective_weights()
+    e = np.asarray(pc.direction)
+    tol, kmax = 1e-12, 64
+    params = torch.tensor(pc.params, dtype=torch.float64, requires_grad=True)
+    E = synth.pulse_samples(params, pc)
+    ctx.objective_forward(psi0, E.detach().numpy(), w, e, pc.dt, pc.ckpt_every, tol, kmax)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = tdks.DipoleObjective.apply(E, ctx, psi0, w, e, pc.dt, pc.ckpt_every, tol, kmax, tdks.FP64, 12)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = params.grad.numpy().copy()
+    fd = np.zeros_like(g)
+    for k in range(len(g)):
+        pp, pm = pc.params.copy(), pc.params.copy()
+        pp[k] += pc.fd_h
+        pm[k] -= pc.fd_h
+        Jp = ctx.objective_forward(psi0, synth.pulse_samples(pp, pc), w, e, pc.dt, pc.ckpt_every, tol, kmax)[0]
+        Jm = ctx.objective_forward(psi0, synth.pulse_samples(pm, pc), w, e, pc.dt, pc.ckpt_every, tol, kmax)[0]
+        fd[k] = (Jp - Jm) / (2 * pc.fd_h)
+    ctx.close()
+    return {"workload": "atom_soft_Z2_6x6x6_p4 driven by 4 Gaussian pulses (omega 0.3, sigma 5, "
+                        "t_j = 4j), 200 steps dt 0.1, checkpoints every 20, Krylov tol 1e-12, "
+                        "12-point Gauss-Legendre Frechet quadrature",
+            "J": J.item(), "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "backward_over_forward": (t2 - t1) / (t1 - t0),
+            "grad_vs_central_fd_max_rel": float(np.abs(g - fd).max() / np.abs(fd).max()),
+            "grad": g.tolist()}
 
 
 def batched_section(tdks, torch, args, local_rank: int) -> dict:
