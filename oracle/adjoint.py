@@ -76,9 +76,13 @@ def gauss_legendre_01(n):
     return 0.5 * (x + 1.0), 0.5 * w
 
 
-def frechet_v(mesh, v_q, psi, lam, tau, tol=1e-12, k_max=200, n_s=12):
-    """dJ/dv(x_q) of Re<lam, exp(-i tau Hbar[v]) psi> (summed over orbitals)."""
-    H = lambda x: ham.apply_H(mesh, v_q, x)
+def frechet_v(mesh, v_q, psi, lam, tau, tol=1e-12, k_max=200, n_s=12, nl=None):
+    """dJ/dv(x_q) of Re<lam, exp(-i tau Hbar[v]) psi> (summed over orbitals); nl: an
+    optional v-independent nonlocal term of Hbar."""
+    if nl is None:
+        H = lambda x: ham.apply_H(mesh, v_q, x)
+    else:
+        H = lambda x: ham.apply_H(mesh, v_q, x) + nl.apply(x)
     wq = mesh.quad_weights()
     g = np.zeros((mesh.n_elem, mesh.nq ** 3))
     for s, ws in zip(*gauss_legendre_01(n_s)):
@@ -111,7 +115,7 @@ def objective_and_gradient(prop, psi0, E, w, e, dt, n_s=12, tol_adj=1e-12):
     xq = mesh.quad_coords()
     wq = mesh.quad_weights()
     ex = xq @ e
-    H = lambda v: (lambda x: ham.apply_H(mesh, v, x))
+    H = prop.hbar
     lam = np.zeros_like(psi0, dtype=complex)
     gh1 = np.zeros((mesh.n_elem, mesh.nq ** 3))
     gh2 = np.zeros_like(gh1)
@@ -122,12 +126,13 @@ def objective_and_gradient(prop, psi0, E, w, e, dt, n_s=12, tol_adj=1e-12):
         g_rho = hxc_adjoint(mesh, r["rho_new"], gh1, hb, xcb) + 2.0 * w[n + 1] * (e @ r["d"]) * wq * ex
         lam = lam + density_adjoint(mesh, r["psi_new"], g_rho, prop.occ)
         gh1_next = gh2.copy()
-        g_vmid = frechet_v(mesh, r["v_mid"], r["psi_prev"], lam, dt, tol_adj, n_s=n_s)
+        g_vmid = frechet_v(mesh, r["v_mid"], r["psi_prev"], lam, dt, tol_adj, n_s=n_s, nl=prop.nl)
         lam_prev, _ = expm_lanczos(H(r["v_mid"]), lam, -dt, tol_adj, 200)
         dJdE[n, 1] = -np.einsum("eq,eqd->d", g_vmid, xq)
         lam_h = density_adjoint(mesh, r["psi_half"], hxc_adjoint(mesh, r["rho_half"], g_vmid, hb, xcb),
                                 prop.occ)
-        g_vpred = frechet_v(mesh, r["v_pred"], r["psi_prev"], lam_h, 0.5 * dt, tol_adj, n_s=n_s)
+        g_vpred = frechet_v(mesh, r["v_pred"], r["psi_prev"], lam_h, 0.5 * dt, tol_adj, n_s=n_s,
+                            nl=prop.nl)
         lam_prev = lam_prev + expm_lanczos(H(r["v_pred"]), lam_h, -0.5 * dt, tol_adj, 200)[0]
         dJdE[n, 0] = -np.einsum("eq,eqd->d", g_vpred, xq)
         gh1 = gh1_next + 1.25 * g_vpred

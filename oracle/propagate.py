@@ -63,8 +63,9 @@ def kick(mesh: Mesh, psibar: np.ndarray, kappa: float, direction) -> np.ndarray:
 
 class Propagator:
     def __init__(self, mesh: Mesh, v_nuc: np.ndarray, occ, hartree=True, use_xc=True,
-                 cg_tol=1e-13, tol=1e-10, k_max=64):
+                 cg_tol=1e-13, tol=1e-10, k_max=64, nl=None):
         self.mesh = mesh
+        self.nl = nl            # optional nonlocal (Kleinman-Bylander) term, Eq. 6
         self.v_nuc = v_nuc
         self.occ = np.asarray(occ, float)
         self.hartree_on = hartree
@@ -107,9 +108,14 @@ class Propagator:
         self.vhxc_2 = v0
         return ham.dipole(self.mesh, rho0)
 
+    def hbar(self, v_q):
+        """x -> Hbar x with the local potential v_q (and the nonlocal term if set)."""
+        if self.nl is None:
+            return lambda x: ham.apply_H(self.mesh, v_q, x)
+        return lambda x: ham.apply_H(self.mesh, v_q, x) + self.nl.apply(x)
+
     def expm(self, v_q, psibar, tau, k_fixed=None):
-        return expm_lanczos(lambda x: ham.apply_H(self.mesh, v_q, x), psibar, tau,
-                            self.tol, self.k_max, k_fixed=k_fixed)
+        return expm_lanczos(self.hbar(v_q), psibar, tau, self.tol, self.k_max, k_fixed=k_fixed)
 
     def magnus_step(self, psibar, dt, E_quarter=(0, 0, 0), E_half=(0, 0, 0),
                     k_fixed=None, record=False):
@@ -136,7 +142,7 @@ class Propagator:
         """Total energy sum_a f_a <psibar_a|T + V_N + V_field|psibar_a> + E_H + E_xc."""
         rho = ham.density(self.mesh, psibar, self.occ)
         vext = self.v_nuc + self.v_field(E)
-        hpsi = ham.apply_H(self.mesh, vext, psibar)
+        hpsi = self.hbar(vext)(psibar)
         e1 = float(np.sum(self.occ * np.einsum("an,an->a", psibar.conj(), hpsi).real))
         eh = 0.0
         if self.hartree_on:

@@ -212,6 +212,17 @@ def pulse_samples(params, pc: PulseConfig):
     return (e[..., None] * d).reshape(pc.n_steps, 6)
 
 
+@dataclasses.dataclass
+class KBParams:
+    """Synthetic Kleinman-Bylander projectors (stand-ins for tabulated pseudopotential
+    data) on every atom of a system: u_lm = exp(-d^2/(2 a^2)) Y_lm(d), Y_00 = 1,
+    Y_1m = d_x, d_y, d_z; dV_l = c_l exp(-d^2/(2 b^2)); l = 0..lmax."""
+    a: float = 1.0
+    b: float = 0.8
+    c: tuple = (-2.0, -1.0)
+    lmax: int = 1
+
+
 BATCH_SEED = 18101305
 
 
