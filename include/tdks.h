@@ -199,6 +199,26 @@ tdks_status tdks_propagate_host(tdks_ctx* ctx, const double* psi_host_in,
                                 double dt, const double* E_host, double tol, int k_max,
                                 int prec, double* dipole_host);
 
+/* Nonlocal pseudopotential term in the Kleinman-Bylander form (Eq. 6):
+ *   V_nl phi = sum_p [int chi_p phi / h_p] chi_p,  chi_p = dV_l u_lm,  h_p = int u_lm dV_l u_lm,
+ * discretized as Hbar_nl = M^-1/2 P D P^T M^-1/2 with P[j][p] = int chi_p N_j and
+ * D = diag(1/h_p), all integrals by the Gauss rule (Sec. VI.A).  Synthetic projectors on
+ * n_atoms atoms at R_host ([n_atoms][3], bohr), with d = r - R:
+ *   u_lm = exp(-|d|^2 / (2 a^2)) Y_lm(d),  Y_00 = 1, Y_1m = d_x, d_y, d_z  (l <= lmax),
+ *   dV_l = c[l] exp(-|d|^2 / (2 b^2)),
+ * projectors ordered atom by atom, l = 0 then d_x, d_y, d_z.  After the call every
+ * Hbar application of the context (tdks_apply_H, tdks_expm, tdks_magnus_step, the
+ * objective and its adjoint) includes Hbar_nl; n_atoms = 0 removes it.  Each atom's
+ * projector columns are stored on the box of nodes where some entry exceeds 1e-16 of
+ * the column maximum.  lmax in {0, 1}; a, b > 0.  Synchronizes.  The batched engine
+ * does not take this term.
+ * tdks_kb_info: projector count, the denominators h_p (h_host, n_proj doubles, may be
+ * NULL), the number of nodes covered by some box and the stored values. */
+tdks_status tdks_set_kb(tdks_ctx* ctx, int n_atoms, const double* R_host, double a, double b,
+                        const double c[2], int lmax);
+tdks_status tdks_kb_info(const tdks_ctx* ctx, int* n_proj, double* h_host, int64_t* n_covered,
+                         int64_t* n_values);
+
 /* Dipole-response objective and its gradient with respect to the field (the
  * adjoint of Secs. VI.B and V; the paper optimizes nothing, this is the reverse
  * mode of its propagation).

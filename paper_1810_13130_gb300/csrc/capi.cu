@@ -59,6 +59,7 @@ tdks_status upload(tdks_ctx* c, T** p, const std::vector<T>& h) {
 }
 
 void free_ctx(tdks_ctx* c) {
+  kb_free(c);
   if (!c) return;
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->d_brk[d]);

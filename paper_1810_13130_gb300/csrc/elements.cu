@@ -960,11 +960,15 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
                  : std::is_same<T, float>::value ? (const T*)c->d_tabf
                                                  : (const T*)c->d_tabdf;
   const Geom g = tdks_geom(c);
+  if (c->kb) TDKS_TRY(kb_project(c, a));
   k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
-  if (a.lanczos && a.kry && a.part)
+  if (a.lanczos && a.kry && a.part) {
     k_alpha<<<a.n_orb, 256, 0, c->stream>>>(a.kry, a.part, a.part_stride, bpe, a.kj);
+    if (c->kb) TDKS_TRY(kb_alpha(c, a));
+  }
   const int gx = assemble_blocks(c, a.n_orb);
   k_assemble<T><<<dim3(gx, a.n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  if (c->kb) TDKS_TRY(kb_add(c, a));
   c->n_launch += (a.lanczos && a.kry && a.part) ? 3 : 2;
   c->n_apply_launch += 1;
   TDKS_CU(c, cudaGetLastError());

@@ -313,7 +313,7 @@ __device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, 
 }
 
 __global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double* npart,
-                          int64_t npstride, int nb) {
+                          int64_t npstride, int nb, const double* xpart, int nx) {
   __shared__ ChebWork W;
   const int o = blockIdx.x;
   const int lane = threadIdx.x;
@@ -321,6 +321,7 @@ __global__ void k_kry_exp(int j, int kmax, double tol, KryOrb* kry, const double
   if (K.status != KRY_ACTIVE) return;
   double v = 0.0;
   for (int k = lane; k < nb; k += 32) v += npart[(long long)o * npstride + k];
+  for (int k = lane; k < nx; k += 32) v += xpart[(long long)o * nx + k];   // nonlocal correction
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   kry_decide(K, j, kmax, tol, sqrt(v), W);
 }
@@ -657,7 +658,8 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
       TDKS_TRY(launch_hbar_apply(c, a, prec));
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
       c->n_apply_units += (int64_t)n_active * c->n_elem;
-      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm);
+      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm, kb_norm_parts(c),
+                                             kb_norm_blocks(c));
       c->n_launch += 1;
       TDKS_CU(c, cudaGetLastError());
       TDKS_TRY(read_summary(c, kry, n_orb, h.data()));

@@ -109,6 +109,7 @@ struct tdks_ctx {
   int* h_int = nullptr;
   bool propagation_ready = false;
   void* adj = nullptr;          // objective / adjoint state (adjoint.cu)
+  void* kb = nullptr;           // nonlocal Kleinman-Bylander projectors (kb.cu)
   // counters
   int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0;
   double apply_ms = 0.0;
@@ -309,3 +310,11 @@ tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, 
 tdks_status dipole_graph(tdks_ctx* c, const double* rho, double* base, const int* step,
                          int64_t step_stride);
 cudaError_t launch_counter_add(int* counter, int inc, cudaStream_t st);
+
+// kb.cu: nonlocal Kleinman-Bylander term, hooked into the Hbar application
+void kb_free(tdks_ctx* c);
+tdks_status kb_project(tdks_ctx* c, const ApplyArgs& a);   // C = Pbar^T (s_j) in
+tdks_status kb_alpha(tdks_ctx* c, const ApplyArgs& a);     // alpha_j += sum |C|^2 / h
+tdks_status kb_add(tdks_ctx* c, const ApplyArgs& a);       // out += Pbar D C (+ norm partials)
+int kb_norm_blocks(const tdks_ctx* c);                      // partials of the Lanczos correction
+const double* kb_norm_parts(const tdks_ctx* c);             // [n_orb][kb_norm_blocks]

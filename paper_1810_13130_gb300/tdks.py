@@ -95,6 +95,8 @@ def lib():
         "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
         "tdks_objective_forward": [v, p, i, i, d, _dp, _dp, _dp, i, d, i, i, _dp, _dp],
         "tdks_objective_backward": [v, i, _dp],
+        "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
+        "tdks_kb_info": [v, C.POINTER(i), _dp, C.POINTER(i64), C.POINTER(i64)],
         "tdks_batch_create": [i, p, p, _dp, i, d, i, C.POINTER(C.c_void_p)],
         "tdks_batch_destroy": [v],
         "tdks_batch_stream": [v],
@@ -128,7 +130,8 @@ def exported_symbols() -> list:
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
-                        "tdks_objective_backward", "tdks_batch_create", "tdks_batch_destroy",
+                        "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info",
+                        "tdks_batch_create", "tdks_batch_destroy",
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
                         "tdks_batch_tune", "tdks_batch_steps", "tdks_batch_stats",
@@ -340,6 +343,23 @@ class Context:
             None if Eh is None else Eh.ctypes.data, tol, k_max, prec, dip.ctypes.data),
             "tdks_propagate_host")
         return dip[:n_steps]
+
+    def set_kb(self, R, a: float = 1.0, b: float = 0.8, c=(-2.0, -1.0), lmax: int = 1):
+        """Kleinman-Bylander projectors on the atoms at R ([n_atoms, 3]); R empty removes them."""
+        Rh = _darr(R).reshape(-1)
+        ch = _darr(c).reshape(2)
+        self._sync_stream()
+        self._check(lib().tdks_set_kb(self.h, len(Rh) // 3, _ptr(Rh) if len(Rh) else None, a, b,
+                                      _ptr(ch), lmax), "tdks_set_kb")
+
+    def kb_info(self) -> dict:
+        n = C.c_int()
+        self._check(lib().tdks_kb_info(self.h, C.byref(n), None, None, None), "tdks_kb_info")
+        h = np.zeros(max(n.value, 1))
+        nc, nv = C.c_int64(), C.c_int64()
+        self._check(lib().tdks_kb_info(self.h, C.byref(n), _ptr(h), C.byref(nc), C.byref(nv)),
+                    "tdks_kb_info")
+        return {"n_proj": n.value, "h": h[:n.value], "n_covered": nc.value, "n_values": nv.value}
 
     def objective_forward(self, psi0: torch.Tensor, E: np.ndarray, w, e, dt: float,
                           ckpt_every: int = 10, tol: float = 1e-10, k_max: int = 64,
