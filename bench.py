@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-system batched runs")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-nonlocal", dest="nonlocal_kb", action="store_false",
+                    help="skip the molecule run with Kleinman-Bylander projectors")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the adjoint-gradient timing on the pulse workload")
     ap.add_argument("--apply-only", action="store_true",
@@ -375,6 +377,8 @@ def ours(args, rank: int, world: int, local_rank: int):
                            "speedup_vs_fp64": v2 / value,
                            "dipole_rel_err": float(np.abs(dm[:, 2] - d64[:, 2]).max() / ind)}
         line["mixed"] = mixed
+    if args.nonlocal_kb and args.prec == "fp64":
+        line["nonlocal"] = nonlocal_section(tdks, torch, cfg, psi0, args, value)
     if args.batched and args.prec == "fp64":
         line["batched"] = batched_section(tdks, torch, args, local_rank)
     if args.adjoint and args.prec == "fp64":
@@ -389,6 +393,39 @@ def ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def nonlocal_section(tdks, torch, cfg, psi0, args, value_local: float) -> dict:
+    """The molecule workload with Kleinman-Bylander projectors (l <= 1, 4 per atom) on
+    its 8 atoms: FP64 step rate against the same steps without them."""
+    import synth
+    kp = synth.KBParams()
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_cg(1e-10)
+    ctx.set_kb(cfg.atom_R, kp.a, kp.b, kp.c, kp.lmax)
+    info = ctx.kb_info()
+    psi = torch.from_numpy(psi0).cuda()
+    ctx.kick(psi, cfg.kick, cfg.kick_dir)
+    ctx.init_propagation(psi)
+    K = max(3, args.steps // 2)
+    for _ in range(args.warmup):
+        ctx.magnus_step(psi, cfg.dt, tol=cfg.tol, k_max=cfg.k_max)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = [ctx.magnus_step(psi, cfg.dt, tol=cfg.tol, k_max=cfg.k_max) for _ in range(K)]
+    ev1.record()
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    ctx.close()
+    v = cfg.n_orb * K / t
+    return {"workload": "molecule workload + Kleinman-Bylander projectors on its 8 atoms "
+                        f"(a {kp.a}, b {kp.b}, c {list(kp.c)}, lmax {kp.lmax})",
+            "n_proj": info["n_proj"], "covered_nodes": info["n_covered"],
+            "stored_values": info["n_values"], "value": v, "unit": "orbital-steps/s",
+            "ms_per_step": 1e3 * t / K, "steps": K,
+            "k_full_max": max(s["k_full_max"] for s in st),
+            "rate_vs_local_only": v / value_local}
 
 
 def adjoint_section(tdks, torch) -> dict:

