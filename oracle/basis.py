@@ -111,3 +111,26 @@ def lagrange_tables(p: int, nq: int):
                 B[q, i] = float(val)
                 D[q, i] = float(der)
     return B, D
+
+
+@functools.lru_cache(maxsize=None)
+def gll_derivative(p: int):
+    """Dn[q][i] = l_i'(xi_q): derivatives of the GLL Lagrange basis at the GLL nodes
+    themselves (the basis values there are the identity)."""
+    _, _, xi, _ = gll(p)
+    Dn = np.zeros((p + 1, p + 1))
+    with mp.workdps(_DPS):
+        for q in range(p + 1):
+            x = xi[q]
+            for i in range(p + 1):
+                der = mp.mpf(0)
+                for l in range(p + 1):
+                    if l == i:
+                        continue
+                    term = 1 / (xi[i] - xi[l])
+                    for m in range(p + 1):
+                        if m != i and m != l:
+                            term *= (x - xi[m]) / (xi[i] - xi[m])
+                    der += term
+                Dn[q, i] = float(der)
+    return Dn
