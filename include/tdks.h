@@ -219,6 +219,30 @@ tdks_status tdks_set_kb(tdks_ctx* ctx, int n_atoms, const double* R_host, double
 tdks_status tdks_kb_info(const tdks_ctx* ctx, int* n_proj, double* h_host, int64_t* n_covered,
                          int64_t* n_values);
 
+/* Self-consistent midpoint step (Sec. VI.B, the fully consistent approach that the
+ * predictor-corrector of tdks_magnus_step replaces): starting from
+ * V_mid = 1.5 V_HXC^{n-1} - 0.5 V_HXC^{n-2}, repeat
+ *   psi^n = exp(-i dt Hbar[V_N + V_mid - E_half . r]) psi^{n-1}, V_HXC^n from rho(psi^n),
+ *   V_mid <- (V_HXC^{n-1} + V_HXC^n) / 2
+ * until the largest change of V_mid is <= sc_tol (at most sc_maxit exponentials, else
+ * TDKS_ERR_NOT_CONVERGED).  E_half: field at t + dt/2 (host).  *iters = exponentials
+ * taken.  Needs tdks_init_propagation; updates the history like tdks_magnus_step.
+ * Synchronizes once per iteration. */
+tdks_status tdks_magnus_step_sc(tdks_ctx* ctx, double* psi_dev, int n_orb, double dt,
+                                const double E_half[3], double tol, int k_max, int prec,
+                                double sc_tol, int sc_maxit, tdks_stats* stats, int* iters);
+
+/* Absorption spectrum (Sec. VII): for a dipole series dip_host ([n_t][3], d(t_n),
+ * t_n = n dt) after a kick psi(0) = exp(-i kappa r.dir) psi_GS,
+ *   alpha(omega) = -(1/kappa) sum_n w_n exp(i omega t_n) g(t_n) (d(t_n) - d(0)) . dir/|dir|
+ * (trapezoid weights w_n, window g(t) = exp(-window t^2)) into alpha_host ([n_om] complex
+ * (re, im), may be NULL) and S(omega) = (2 omega / 3 pi) Im alpha(omega) into S_host
+ * ([n_om], may be NULL); summing S over kicks along x, y, z gives the trace.  All
+ * arrays are host memory; computed on the current device.  Synchronizes. */
+tdks_status tdks_spectrum(const double* dip_host, int n_t, double dt, double kappa,
+                          const double dir[3], double window, const double* omega_host, int n_om,
+                          double* alpha_host, double* S_host);
+
 /* Dipole-response objective and its gradient with respect to the field (the
  * adjoint of Secs. VI.B and V; the paper optimizes nothing, this is the reverse
  * mode of its propagation).

@@ -112,24 +112,6 @@ void free_ctx(tdks_ctx* c) {
 }
 
 // V_HXC = V_H[rho] + V_XC[rho] of the orbitals psi; rho left in c->d_rho.
-tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters) {
-  const size_t nf = (size_t)(c->n_elem * c->nq3);
-  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
-  if (c->hartree) {
-    TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters));
-  } else {
-    TDKS_CU(c, cudaMemsetAsync(c->d_vh, 0, nf * sizeof(double), c->stream));
-    if (cg_iters) *cg_iters = 0;
-  }
-  if (c->xc) {
-    TDKS_TRY(launch_xc(c, c->d_rho, c->d_vtmp));
-    TDKS_TRY(launch_combine(c, out, c->d_vh, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, nullptr));
-  } else {
-    TDKS_CU(c, cudaMemcpyAsync(out, c->d_vh, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  }
-  return TDKS_OK;
-}
-
 // Folded storage of a centrosymmetric n x n matrix (layout in tdks_internal.h).
 void fold_centrosymmetric(const double* M, int n, double* out) {
   const int h = n / 2;
@@ -152,6 +134,25 @@ tdks_status check_orb(tdks_ctx* c, int n_orb) {
 }
 
 }  // namespace
+
+tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters) {
+  const size_t nf = (size_t)(c->n_elem * c->nq3);
+  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
+  if (c->hartree) {
+    TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters));
+  } else {
+    TDKS_CU(c, cudaMemsetAsync(c->d_vh, 0, nf * sizeof(double), c->stream));
+    if (cg_iters) *cg_iters = 0;
+  }
+  if (c->xc) {
+    TDKS_TRY(launch_xc(c, c->d_rho, c->d_vtmp));
+    TDKS_TRY(launch_combine(c, out, c->d_vh, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, nullptr));
+  } else {
+    TDKS_CU(c, cudaMemcpyAsync(out, c->d_vh, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return TDKS_OK;
+}
+
 
 // vhxc_of for stream capture (fixed-length Poisson CG, no host reads)
 tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter, int* err) {

@@ -302,6 +302,8 @@ cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, 
                                  cudaStream_t st);
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
                               unsigned long long* dof_applies, int* kseen, cudaStream_t st);
+// V_HXC of an orbital block (density, Hartree by the polling CG, LDA) into out (capi.cu)
+tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters);
 // capturable forms of the per-system field work (no host synchronization)
 tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err);
 tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err);

@@ -96,6 +96,8 @@ def lib():
         "tdks_objective_forward": [v, p, i, i, d, _dp, _dp, _dp, i, d, i, i, _dp, _dp],
         "tdks_objective_backward": [v, i, _dp],
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
+        "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
+        "tdks_spectrum": [_dp, i, d, d, _dp, d, _dp, i, _dp, _dp],
         "tdks_kb_info": [v, C.POINTER(i), _dp, C.POINTER(i64), C.POINTER(i64)],
         "tdks_batch_create": [i, p, p, _dp, i, d, i, C.POINTER(C.c_void_p)],
         "tdks_batch_destroy": [v],
@@ -131,6 +133,7 @@ def exported_symbols() -> list:
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info",
+                        "tdks_magnus_step_sc", "tdks_spectrum",
                         "tdks_batch_create", "tdks_batch_destroy",
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
@@ -344,6 +347,20 @@ class Context:
             "tdks_propagate_host")
         return dip[:n_steps]
 
+    def magnus_step_sc(self, psi: torch.Tensor, dt: float, E_half=(0, 0, 0), tol: float = 1e-10,
+                       k_max: int = 64, prec: int = FP64, sc_tol: float = 1e-10,
+                       sc_maxit: int = 50) -> dict:
+        eh = _darr(E_half)
+        st = Stats()
+        it = C.c_int()
+        self._sync_stream()
+        self._check(lib().tdks_magnus_step_sc(self.h, _dev(psi, torch.complex128, "psi"), psi.shape[0],
+                                              dt, _ptr(eh), tol, k_max, prec, sc_tol, sc_maxit,
+                                              C.byref(st), C.byref(it)), "tdks_magnus_step_sc")
+        out = st.as_dict()
+        out["iterations"] = it.value
+        return out
+
     def set_kb(self, R, a: float = 1.0, b: float = 0.8, c=(-2.0, -1.0), lmax: int = 1):
         """Kleinman-Bylander projectors on the atoms at R ([n_atoms, 3]); R empty removes them."""
         Rh = _darr(R).reshape(-1)
@@ -429,6 +446,21 @@ def _descs(cfg, keep):
                    _ptr(Zc) if len(Zc) else None, NUC_KIND[cfg.nuc_kind], float(cfg.nuc_param),
                    int(bool(cfg.hartree)), int(bool(cfg.xc)))
     return m, s
+
+
+def spectrum(dip, dt: float, kappa: float, direction, window: float, omega):
+    """(alpha(omega) complex array, S(omega)) of a kicked dipole series (tdks_spectrum)."""
+    d = _darr(dip).reshape(-1, 3)
+    di = _darr(direction).reshape(3)
+    om = _darr(omega).reshape(-1)
+    a = np.zeros(2 * len(om))
+    S = np.zeros(len(om))
+    torch.cuda.current_stream().synchronize()
+    st = lib().tdks_spectrum(_ptr(d), d.shape[0], dt, kappa, _ptr(di), window, _ptr(om), len(om),
+                             _ptr(a), _ptr(S))
+    if st != 0:
+        raise TDKSError(f"tdks_spectrum: {lib().tdks_status_string(st).decode()}")
+    return a[0::2] + 1j * a[1::2], S
 
 
 class Batch:
