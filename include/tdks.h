@@ -219,6 +219,18 @@ tdks_status tdks_set_kb(tdks_ctx* ctx, int n_atoms, const double* R_host, double
 tdks_status tdks_kb_info(const tdks_ctx* ctx, int* n_proj, double* h_host, int64_t* n_covered,
                          int64_t* n_values);
 
+/* GLL-collocation variant of Hbar (not the paper's operator: every integral of H by
+ * the GLL rule on the element nodes instead of the Gauss rule of Sec. VI.A):
+ *   out = M^-1/2 K_gll M^-1/2 psi + v_nodes .* psi,
+ * K_gll per element = sum_d c_d (K1 along d) (x) W_l (x) W_l with the exact 1-D stiffness
+ * K1 and the GLL weights W_l (transverse mass lumped); the potential is diagonal in
+ * the Loewdin basis.  v_nodes_dev: V at the interior nodes ([n_int], device, e.g. from
+ * tdks_nuclear_potential_nodes).  FP64.  psi_dev and out_dev must not overlap. */
+tdks_status tdks_apply_H_gll(tdks_ctx* ctx, const double* psi_dev, const double* v_nodes_dev,
+                             double* out_dev, int n_orb);
+/* V_N at the interior nodes ([n_int], device). */
+tdks_status tdks_nuclear_potential_nodes(tdks_ctx* ctx, double* v_nodes_dev);
+
 /* Self-consistent midpoint step (Sec. VI.B, the fully consistent approach that the
  * predictor-corrector of tdks_magnus_step replaces): starting from
  * V_mid = 1.5 V_HXC^{n-1} - 0.5 V_HXC^{n-2}, repeat

@@ -295,6 +295,9 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
     fold_centrosymmetric(t.B.data(), P1, &tab[tab_off_csB(P1)]);
     fold_centrosymmetric(Bt.data(), P1, &tab[tab_off_csBT(P1)]);
     fold_centrosymmetric(t.Kq.data(), P1, &tab[tab_off_csK(P1)]);
+    // GLL-collocation variant: GLL weights and the folded 1-D stiffness K1 = D^T W D
+    std::memcpy(&tab[tab_off_wl(P1)], t.w.data(), P1 * sizeof(double));
+    fold_centrosymmetric(t.K1.data(), P1, &tab[tab_off_csK1(P1)]);
   }
   std::vector<float> tabf(tab.begin(), tab.end());
   std::vector<float> tabdf(2 * tab.size());
@@ -393,6 +396,18 @@ tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb,
               0, nullptr, 0, nullptr, 0, 0};
   c->n_apply_units += (int64_t)n_orb * c->n_elem;
   return launch_hbar_apply(c, a, prec);
+}
+
+tdks_status tdks_nuclear_potential_nodes(tdks_ctx* c, double* v_nodes) {
+  if (!c || !v_nodes) return TDKS_ERR_ARG;
+  return launch_nuclear_nodes(c, v_nodes);
+}
+
+tdks_status tdks_apply_H_gll(tdks_ctx* c, const double* psi, const double* v_nodes, double* out,
+                             int n_orb) {
+  if (!c || !psi || !v_nodes || !out) return TDKS_ERR_ARG;
+  if (n_orb < 1) return tdks_fail(c, TDKS_ERR_ARG, "n_orb >= 1");
+  return launch_hbar_gll(c, (const double2*)psi, v_nodes, (double2*)out, n_orb);
 }
 
 tdks_status tdks_density(tdks_ctx* c, const double* psi, int n_orb, double* rho) {

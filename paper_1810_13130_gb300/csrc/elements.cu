@@ -380,6 +380,119 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
 }
 
 // ---------------------------------------------------------------------------
+// GLL-collocation variant: every integral of H by the GLL rule on the element nodes.
+// Kinetic: sum_d c_d (K1 along d) x W_l x W_l (W_l: GLL weights; K1 = D^T W D is the
+// exact 1-D stiffness, so only the transverse mass is lumped); the potential is the
+// diagonal V(x_j) in the Loewdin basis and is added after the assembly.  Three
+// one-dimensional contractions per element and component (folded K1).
+// ---------------------------------------------------------------------------
+template <int P1>
+__global__ void __launch_bounds__(256, 2) k_hbar_gll(Geom g, const double* __restrict__ tab,
+                                                  const double2* __restrict__ in, int64_t stride,
+                                                  int n_orb, int orb_per_cta, Cx<double>* __restrict__ ev) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  typedef Cx<double> V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* sK = reinterpret_cast<double*>(smem);
+  double* swl = sK + CS;
+  const size_t off = ((CS + P1) * sizeof(double) + 15) & ~size_t(15);
+  V* S1 = reinterpret_cast<V*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  V* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < CS; i += nthr) sK[i] = tab[tab_off_csK1(P1) + i];
+  for (int i = tid; i < P1; i += nthr) swl[i] = tab[tab_off_wl(P1) + i];
+  __syncthreads();
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
+  int ex = 0, ey = 0, ez = 0;
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const bool valid = plain_elem(g, eidx, ex, ey, ez);
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  if (valid) {
+    const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
+    const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
+    const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
+    cx = hy * hz / (4.0 * hx);
+    cy = hx * hz / (4.0 * hy);
+    cz = hx * hy / (4.0 * hz);
+  }
+  const long long plane = (long long)g.nix * g.niy;
+  const int Ig = ex * g.p + u, Jg = ey * g.p + v;
+  const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
+  const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
+  double gsc[P1];
+#pragma unroll
+  for (int c = 0; c < P1; ++c) {
+    const int K = ez * g.p + c;
+    gsc[c] = (inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0;
+  }
+  const int o0 = blockIdx.y * orb_per_cta;
+  const int o1 = min(o0 + orb_per_cta, n_orb);
+  for (int o = o0; o < o1; ++o) {
+    const double2* x = in + (long long)o * stride;
+    V col[P1], t[P1];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      const int K = ez * g.p + c;
+      vzero(col[c]);
+      if (inG && K >= 1 && K <= g.niz) {
+        const double2 w2 = x[baseG + plane * (K - 1)];
+        col[c].re = w2.x * gsc[c];
+        col[c].im = w2.y * gsc[c];
+      }
+    }
+    // z: r = cz Wl_x Wl_y (K1 u)_z  (thread owns the z-line at (x = u, y = v))
+    store_line(col, S1 + v * P1 + u, P2);
+    cs_apply<P1>(sK, col, t);
+    const double fz = cz * swl[u] * swl[v];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) t[c] = vscale(fz, t[c]);
+    store_line(t, S2 + v * P1 + u, P2);
+    __syncthreads();
+    // y: r += cy Wl_x Wl_z (K1 u)_y  (y-line at (x = u, z = v))
+    load_line(col, S1 + v * P2 + u, P1);
+    cs_apply<P1>(sK, col, t);
+    const double fy = cy * swl[u] * swl[v];
+#pragma unroll
+    for (int b = 0; b < P1; ++b) {
+      V r = S2[v * P2 + b * P1 + u];
+      madd(r, fy, t[b]);
+      S2[v * P2 + b * P1 + u] = r;
+    }
+    __syncthreads();
+    // x: r += cx Wl_y Wl_z (K1 u)_x  (x-line at (y = u, z = v)); element result
+    load_line(col, S1 + v * P2 + u * P1, 1);
+    cs_apply<P1>(sK, col, t);
+    const double fx = cx * swl[u] * swl[v];
+#pragma unroll
+    for (int a2 = 0; a2 < P1; ++a2) {
+      V r = S2[v * P2 + u * P1 + a2];
+      madd(r, fx, t[a2]);
+      t[a2] = r;
+    }
+    if (valid) store_line(t, ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1, 1);
+    __syncthreads();
+  }
+}
+
+// out += v psi (the collocated potential, diagonal in the Loewdin basis)
+__global__ void k_diag_add(long long n, int n_orb, const double* __restrict__ vn,
+                           const double2* __restrict__ in, double2* __restrict__ out) {
+  const long long tot = n * n_orb;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double f = vn[i % n];
+    const double2 x = in[i];
+    double2 y = out[i];
+    y.x = fma(f, x.x, y.x);
+    y.y = fma(f, x.y, y.y);
+    out[i] = y;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Batched apply: a persistent grid walks the work list of one degree class.
 // Item (sys, eblk, o0, o1): elements [eblk E, eblk E + E) of system sys for the
 // orbitals o0..o1-1 that are in the Lanczos recurrence; each orbital reads its own
@@ -1258,4 +1371,42 @@ cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_
   else if (prec == TDKS_DF64) k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
   else k_bassemble<double><<<n_rows, 128, 0, st>>>(sys, rows);
   return cudaGetLastError();
+}
+
+template <int P1>
+static tdks_status hbar_gll_t(tdks_ctx* c, const double2* psi, const double* vn, double2* out, int n_orb) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  const size_t smem = (((CS + P1) * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
+  TDKS_CU(c, cudaFuncSetAttribute(k_hbar_gll<P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t need = (size_t)n_orb * c->n_elem * P3 * sizeof(Cx<double>);
+  if (need > c->evec_bytes) {
+    cudaFree(c->d_evec);
+    c->d_evec = nullptr;
+    c->evec_bytes = 0;
+    if (cudaMalloc(&c->d_evec, need) != cudaSuccess) {
+      cudaGetLastError();
+      return tdks_fail(c, TDKS_ERR_NOMEM, "element-result buffer");
+    }
+    c->evec_bytes = need;
+  }
+  Cx<double>* ev = static_cast<Cx<double>*>(c->d_evec);
+  const int bpe = elem_blocks_t<P1>(c);
+  int opc = 1;
+  while (opc < n_orb && (long long)bpe * ((n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
+  const Geom g = tdks_geom(c);
+  k_hbar_gll<P1><<<dim3(bpe, (n_orb + opc - 1) / opc), dim3(P2, E), smem, c->stream>>>(g, c->d_tab, psi, c->n_int,
+                                                                                   n_orb, opc, ev);
+  ApplyArgs a{psi, c->n_int, out, c->n_int, n_orb, nullptr, 0, nullptr, 0, 0, nullptr, 0, nullptr, 0, 0};
+  k_assemble<double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  k_diag_add<<<608, 256, 0, c->stream>>>(c->n_int, n_orb, vn, psi, out);
+  c->n_launch += 3;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+tdks_status launch_hbar_gll(tdks_ctx* c, const double2* psi, const double* v_nodes, double2* out,
+                            int n_orb) {
+  TDKS_DISPATCH(c->P1, (hbar_gll_t<P1>(c, psi, v_nodes, out, n_orb)));
+  return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }

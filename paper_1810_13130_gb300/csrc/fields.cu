@@ -29,31 +29,51 @@ __device__ __forceinline__ void quad_xyz(const Geom& g, const double* eta, int P
   }
 }
 
+// V_N at the point x for the nuclear-potential kinds of tdks_nuc_kind
+__device__ __forceinline__ double nuc_at(const double* x, int kind, double param, int n_nuc,
+                                         const double* R, const double* Z) {
+  double acc = 0.0;
+  if (kind == TDKS_NUC_HARMONIC) {
+    const double dx = x[0] - R[0], dy = x[1] - R[1], dz = x[2] - R[2];
+    acc = 0.5 * param * param * (dx * dx + dy * dy + dz * dz);
+  } else if (kind != TDKS_NUC_NONE) {
+    for (int I = 0; I < n_nuc; ++I) {
+      const double dx = x[0] - R[3 * I], dy = x[1] - R[3 * I + 1], dz = x[2] - R[3 * I + 2];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double r = sqrt(r2);
+      if (kind == TDKS_NUC_SOFT) {
+        acc -= Z[I] / sqrt(r2 + param);
+      } else if (kind == TDKS_NUC_BARE) {
+        acc -= Z[I] / r;
+      } else {  // erf: -Z erf(r/rc)/r, limit 2 Z / (sqrt(pi) rc) at r = 0
+        acc -= (r > 0.0) ? Z[I] * erf(r / param) / r : Z[I] * 2.0 / (sqrt(M_PI) * param);
+      }
+    }
+  }
+  return acc;
+}
+
 __global__ void k_nuclear(Geom g, const double* eta, int P1, long long n, int kind, double param,
                           int n_nuc, const double* R, const double* Z, double* v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     double x[3];
     quad_xyz(g, eta, P1, i, x);
-    double acc = 0.0;
-    if (kind == TDKS_NUC_HARMONIC) {
-      const double dx = x[0] - R[0], dy = x[1] - R[1], dz = x[2] - R[2];
-      acc = 0.5 * param * param * (dx * dx + dy * dy + dz * dz);
-    } else if (kind != TDKS_NUC_NONE) {
-      for (int I = 0; I < n_nuc; ++I) {
-        const double dx = x[0] - R[3 * I], dy = x[1] - R[3 * I + 1], dz = x[2] - R[3 * I + 2];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double r = sqrt(r2);
-        if (kind == TDKS_NUC_SOFT) {
-          acc -= Z[I] / sqrt(r2 + param);
-        } else if (kind == TDKS_NUC_BARE) {
-          acc -= Z[I] / r;
-        } else {  // erf: -Z erf(r/rc)/r, limit 2 Z / (sqrt(pi) rc) at r = 0
-          acc -= (r > 0.0) ? Z[I] * erf(r / param) / r : Z[I] * 2.0 / (sqrt(M_PI) * param);
-        }
-      }
-    }
-    v[i] = acc;
+    v[i] = nuc_at(x, kind, param, n_nuc, R, Z);
+  }
+}
+
+// V_N at the interior nodes (collocated potential of the GLL variant)
+__global__ void k_nuclear_nodes(const double* cx, const double* cy, const double* cz, int nix, int niy,
+                                long long n, int kind, double param, int n_nuc, const double* R,
+                                const double* Z, double* v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(i % nix) + 1;
+    const int J = (int)((i / nix) % niy) + 1;
+    const int K = (int)(i / ((long long)nix * niy)) + 1;
+    const double x[3] = {cx[I], cy[J], cz[K]};
+    v[i] = nuc_at(x, kind, param, n_nuc, R, Z);
   }
 }
 
@@ -324,4 +344,13 @@ tdks_status dipole_graph(tdks_ctx* c, const double* rho, double* base, const int
 cudaError_t launch_counter_add(int* counter, int inc, cudaStream_t st) {
   k_counter_add<<<1, 32, 0, st>>>(counter, inc);
   return cudaGetLastError();
+}
+
+tdks_status launch_nuclear_nodes(tdks_ctx* c, double* v) {
+  k_nuclear_nodes<<<vec_grid(c->n_int), kVecThreads, 0, c->stream>>>(
+      c->d_coord[0], c->d_coord[1], c->d_coord[2], c->Ni[0], c->Ni[1], c->n_int, c->nuc_kind, c->nuc_param,
+      c->n_nuc, c->d_R, c->d_Z, v);
+  c->n_launch += 1;
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
 }

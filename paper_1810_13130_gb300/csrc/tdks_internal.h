@@ -171,7 +171,9 @@ TDKS_HD inline int tab_off_eta(int P1) { return 4 * P1 * P1 + P1; }
 TDKS_HD inline int tab_off_csB(int P1) { return 4 * P1 * P1 + 2 * P1; }
 TDKS_HD inline int tab_off_csBT(int P1) { return tab_off_csB(P1) + cs_size(P1); }
 TDKS_HD inline int tab_off_csK(int P1) { return tab_off_csBT(P1) + cs_size(P1); }
-TDKS_HD inline int tab_size(int P1) { return tab_off_csK(P1) + cs_size(P1); }
+TDKS_HD inline int tab_off_wl(int P1) { return tab_off_csK(P1) + cs_size(P1); }   // GLL weights
+TDKS_HD inline int tab_off_csK1(int P1) { return tab_off_wl(P1) + P1; }            // folded K1
+TDKS_HD inline int tab_size(int P1) { return tab_off_csK1(P1) + cs_size(P1); }
 
 // ---------------------------------------------------------------- launchers
 // element kernels (elements.cu)
@@ -223,6 +225,7 @@ void tdks_sym_eigen(std::vector<double>& C, int n, std::vector<double>& V, std::
 tdks_status launch_fxc_add(tdks_ctx* c, const double* rho, const double* g_h, double* g_rho);
 tdks_status launch_dipole_sens(tdks_ctx* c, double coef, const double e[3], double* g_rho);
 tdks_status launch_nuclear(tdks_ctx* c);
+tdks_status launch_nuclear_nodes(tdks_ctx* c, double* v);   // V_N at the interior nodes
 tdks_status launch_xc(tdks_ctx* c, const double* rho, double* vxc);
 tdks_status run_dipole(tdks_ctx* c, const double* rho, double d[3], int weighted = 1);
 tdks_status launch_kick(tdks_ctx* c, double2* psi, int n_orb, double kappa, const double dir[3]);
@@ -320,3 +323,7 @@ tdks_status kb_alpha(tdks_ctx* c, const ApplyArgs& a);     // alpha_j += sum |C|
 tdks_status kb_add(tdks_ctx* c, const ApplyArgs& a);       // out += Pbar D C (+ norm partials)
 int kb_norm_blocks(const tdks_ctx* c);                      // partials of the Lanczos correction
 const double* kb_norm_parts(const tdks_ctx* c);             // [n_orb][kb_norm_blocks]
+
+// GLL-collocation variant of Hbar (elements.cu): out = M^-1/2 K_gll M^-1/2 psi + v_nodes psi
+tdks_status launch_hbar_gll(tdks_ctx* c, const double2* psi, const double* v_nodes, double2* out,
+                            int n_orb);

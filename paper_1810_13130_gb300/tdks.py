@@ -97,6 +97,8 @@ def lib():
         "tdks_objective_backward": [v, i, _dp],
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
+        "tdks_apply_H_gll": [v, p, p, p, i],
+        "tdks_nuclear_potential_nodes": [v, p],
         "tdks_spectrum": [_dp, i, d, d, _dp, d, _dp, i, _dp, _dp],
         "tdks_kb_info": [v, C.POINTER(i), _dp, C.POINTER(i64), C.POINTER(i64)],
         "tdks_batch_create": [i, p, p, _dp, i, d, i, C.POINTER(C.c_void_p)],
@@ -133,7 +135,8 @@ def exported_symbols() -> list:
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info",
-                        "tdks_magnus_step_sc", "tdks_spectrum",
+                        "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
+                        "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
@@ -359,6 +362,23 @@ class Context:
                                               C.byref(st), C.byref(it)), "tdks_magnus_step_sc")
         out = st.as_dict()
         out["iterations"] = it.value
+        return out
+
+    def nuclear_potential_nodes(self) -> torch.Tensor:
+        out = torch.empty(self.n_int, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        self._check(lib().tdks_nuclear_potential_nodes(self.h, out.data_ptr()),
+                    "tdks_nuclear_potential_nodes")
+        return out
+
+    def apply_H_gll(self, psi: torch.Tensor, v_nodes: torch.Tensor,
+                    out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = torch.empty_like(psi) if out is None else out
+        self._sync_stream()
+        self._check(lib().tdks_apply_H_gll(self.h, _dev(psi, torch.complex128, "psi"),
+                                           _dev(v_nodes, torch.float64, "v_nodes"),
+                                           _dev(out, torch.complex128, "out"), psi.shape[0]),
+                    "tdks_apply_H_gll")
         return out
 
     def set_kb(self, R, a: float = 1.0, b: float = 0.8, c=(-2.0, -1.0), lmax: int = 1):

@@ -73,3 +73,28 @@ def test_spectrum_matches_oracle():
     ref_S = spectrum.strength([(d, direction)], dt, kappa, win, om)
     assert _rel(a, ref_a) < 1e-12
     assert _rel(S, ref_S) < 1e-12
+
+
+@pytest.mark.parametrize("p,n", [(1, (3, 2, 2)), (2, (2, 3, 2)), (4, (2, 2, 3)), (6, (2, 2, 1)), (8, (2, 1, 2))])
+def test_gll_collocation_apply_matches_oracle(p, n):
+    from oracle import collocation as col
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(*n, p=p, n_orb=2, graded=True)
+    m = Mesh.from_config(cfg)
+    ctx = tdks.Context.from_config(cfg)
+    v = synth.random_potential(m.N_int, 9)
+    psi = synth.random_psi(2, m.N_int, 10)
+    out = ctx.apply_H_gll(torch.from_numpy(psi).cuda(), torch.from_numpy(v).cuda())
+    assert _rel(out.cpu().numpy(), col.apply_H_gll(m, v, psi)) < 1e-12
+
+
+def test_nuclear_potential_at_nodes():
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(3, 2, 2, p=4, n_orb=1)
+    m = Mesh.from_config(cfg)
+    ctx = tdks.Context.from_config(cfg)
+    X = m.node_coords()
+    R = np.asarray(cfg.atom_R)[0]
+    ref = -cfg.atom_Z[0] / np.sqrt(np.sum((X - R) ** 2, axis=1) + cfg.nuc_param)
+    got = ctx.nuclear_potential_nodes().cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-14)
