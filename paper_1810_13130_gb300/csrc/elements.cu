@@ -269,14 +269,14 @@ __device__ __forceinline__ int node_elems(int I, int p, int n, int* e, int* loc)
 // contributions in a fixed order and applies the Loewdin scale.  With `lanczos`
 // the three-term update w = Hbar q_j - alpha_j q_j - beta_{j-1} q_{j-1} is fused
 // (ca = alpha_j s_j, cb = beta_{j-1} s_{j-1}) and the sum of |w|^2 over the rows
-// r0, r0 + rstride, ... handled here is returned.
-template <typename T>
-__device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<T>* __restrict__ evo,
+// r0, r0 + rstride, ... handled here is returned.  The degree is a compile-time
+// constant: the node -> (element, local index) split is a multiply-shift.
+template <int P1, typename T>
+__device__ __forceinline__ double assemble_rows(const Geom& g, const Cx<T>* __restrict__ evo,
                                                 const double2* qj, const double2* qm,
                                                 double2* out, double ca, double cb, int lanczos,
                                                 int accumulate, int r0, int rstride) {
-  const int P2 = P1 * P1;
-  const long long P3 = (long long)P2 * P1;
+  constexpr int p = P1 - 1, P2 = P1 * P1, P3 = P2 * P1;
   constexpr bool kF32 = std::is_same<T, float>::value;
   constexpr bool kDF = std::is_same<T, Df>::value;
   const int rows = g.niy * g.niz;
@@ -288,35 +288,58 @@ __device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<
   const int tstep = nix >= nt ? nt : nix;
   double acc = 0.0;
   if (tr >= rpb) return acc;
+  const long long xstride = P3;                             // next element along x
   for (int r = r0 + tr * rstride; r < rows; r += rpb * rstride) {
     const int J = r % g.niy + 1, K = r / g.niy + 1;
-    int ey[2], by[2], ez[2], bz[2], ex[2], bx[2];
-    const int ny = node_elems(J, g.p, g.ny, ey, by);
-    const int nz = node_elems(K, g.p, g.nz, ez, bz);
+    int ey[2], by[2], ez[2], bz[2];
+    const int ny = node_elems(J, p, g.ny, ey, by);
+    const int nz = node_elems(K, p, g.nz, ez, bz);
+    // element rows (y, z) holding this node row, in the order z then y
+    long long base[4] = {0, 0, 0, 0};
+    const int nb = ny * nz;
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+        if (kz < nz && ky < ny)
+          base[kz * ny + ky] = (long long)g.nx * (ey[ky] + (long long)g.ny * ez[kz]) * P3 + bz[kz] * P2 + by[ky] * P1;
     const double syz = g.s[1][J] * g.s[2][K];
     const float syzf = g.sf[1][J] * g.sf[2][K];
     const long long rowbase = (long long)g.nix * (r);
     for (int I = tI + 1; I <= g.nix; I += tstep) {
-      const int nx = node_elems(I, g.p, g.nx, ex, bx);
+      // x: one element inside, two on a shared face (left element first)
+      const int eh = I / p, l = I - eh * p;
+      long long xo[2] = {0, 0};
+      int nxc;
+      if (l != 0) {
+        xo[0] = eh * xstride + l;
+        nxc = 1;
+      } else {
+        nxc = 0;
+        if (eh - 1 >= 0) xo[nxc++] = (eh - 1) * xstride + p;
+        if (eh < g.nx) xo[nxc++] = eh * xstride;
+      }
       double re = 0.0, im = 0.0;
       float fre = 0.f, fim = 0.f;
       Df dre{0.f, 0.f}, dim{0.f, 0.f};
-      for (int kz = 0; kz < nz; ++kz)
-        for (int ky = 0; ky < ny; ++ky)
-          for (int kx = 0; kx < nx; ++kx) {
-            const long long e = ex[kx] + (long long)g.nx * (ey[ky] + (long long)g.ny * ez[kz]);
-            const Cx<T> c = evo[e * P3 + bz[kz] * P2 + by[ky] * P1 + bx[kx]];
-            if constexpr (kF32) {
-              fre += c.re;
-              fim += c.im;
-            } else if constexpr (kDF) {
-              dre = df_add(dre, c.re);
-              dim = df_add(dim, c.im);
-            } else {
-              re += c.re;
-              im += c.im;
-            }
+      // fixed trip counts keep base[] and xo[] in registers
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          if (k >= nb || kx >= nxc) continue;
+          const Cx<T> c = evo[base[k] + xo[kx]];
+          if constexpr (kF32) {
+            fre += c.re;
+            fim += c.im;
+          } else if constexpr (kDF) {
+            dre = df_add(dre, c.re);
+            dim = df_add(dim, c.im);
+          } else {
+            re += c.re;
+            im += c.im;
           }
+        }
       if constexpr (kDF) {
         re = f2d_bits(dre.hi) + f2d_bits(dre.lo);
         im = f2d_bits(dim.hi) + f2d_bits(dim.lo);
@@ -352,9 +375,8 @@ __device__ __forceinline__ double assemble_rows(const Geom& g, int P1, const Cx<
   return acc;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* __restrict__ ev,
-                                                  ApplyArgs a) {
+template <int P1, typename T>
+__global__ void __launch_bounds__(128) k_assemble(Geom g, const Cx<T>* __restrict__ ev, ApplyArgs a) {
   __shared__ double red[4];
   const int o = blockIdx.y;
   double ca = 0.0, cb = 0.0;
@@ -371,8 +393,8 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, int P1, const Cx<T>* _
   const double2* qj = a.in_base + (long long)o * a.in_stride;
   const double2* qm = a.vm_base ? a.vm_base + (long long)o * a.vm_stride : nullptr;
   double2* out = a.out_base + (long long)o * a.out_stride;
-  const double acc = assemble_rows<T>(g, P1, evo, qj, qm, out, ca, cb, a.lanczos, a.accumulate,
-                                      blockIdx.x, gridDim.x);
+  const double acc = assemble_rows<P1, T>(g, evo, qj, qm, out, ca, cb, a.lanczos, a.accumulate,
+                                          blockIdx.x, gridDim.x);
   if (a.npart) {
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) a.npart[(long long)o * a.npart_stride + blockIdx.x] = s;
@@ -593,7 +615,14 @@ __global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
   double2* out = S.Vw + ((long long)w.o * S.kmax + j) * S.n_int;
   const Geom g = S.g;
   const Cx<T>* evo = static_cast<const Cx<T>*>(S.ev) + (long long)w.o * S.n_elem * S.P1 * S.P1 * S.P1;
-  const double acc = assemble_rows<T>(g, S.P1, evo, qj, qm, out, ca, cb, 1, 0, w.rblk, S.n_rblk);
+  double acc = 0.0;
+  switch (S.P1) {   // uniform per block
+#define TDKS_BASM(P) \
+  case P: acc = assemble_rows<P, T>(g, evo, qj, qm, out, ca, cb, 1, 0, w.rblk, S.n_rblk); break;
+    TDKS_BASM(2) TDKS_BASM(3) TDKS_BASM(4) TDKS_BASM(5) TDKS_BASM(6) TDKS_BASM(7) TDKS_BASM(8) TDKS_BASM(9)
+#undef TDKS_BASM
+    default: break;
+  }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) S.npart[(long long)w.o * S.n_rblk + w.rblk] = s;
 }
@@ -1080,7 +1109,7 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
     if (c->kb) TDKS_TRY(kb_alpha(c, a));
   }
   const int gx = assemble_blocks(c, a.n_orb);
-  k_assemble<T><<<dim3(gx, a.n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  k_assemble<P1, T><<<dim3(gx, a.n_orb), 128, 0, c->stream>>>(g, ev, a);
   if (c->kb) TDKS_TRY(kb_add(c, a));
   c->n_launch += (a.lanczos && a.kry && a.part) ? 3 : 2;
   c->n_apply_launch += 1;
@@ -1184,7 +1213,7 @@ tdks_status dens_adj_t(tdks_ctx* c, const double2* psi, int n_orb, const double*
       g, c->d_tab, psi, c->n_int, n_orb, c->d_occ, grho, ev);
   ApplyArgs a{psi, c->n_int, lam, c->n_int, n_orb, nullptr, 0, nullptr, 0, 0, nullptr, 0, nullptr, 0,
               accumulate};
-  k_assemble<double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  k_assemble<P1, double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, ev, a);
   c->n_launch += 2;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
@@ -1228,8 +1257,10 @@ int stiff_blocks_per_color(const tdks_ctx* c) {
 
 int assemble_blocks(const tdks_ctx* c, int n_orb) {
   const int rows = c->Ni[1] * c->Ni[2];
-  int gx = 2048 / (n_orb > 0 ? n_orb : 1);
-  if (gx < 64) gx = 64;
+  // several waves of 128-thread blocks over all orbitals, so the last partial wave is
+  // a small share of the launch (at most 2048 partials per orbital)
+  int gx = 8192 / (n_orb > 0 ? n_orb : 1);
+  if (gx < 128) gx = 128;
   if (gx > 2048) gx = 2048;
   return rows < gx ? rows : gx;
 }
@@ -1398,7 +1429,7 @@ static tdks_status hbar_gll_t(tdks_ctx* c, const double2* psi, const double* vn,
   k_hbar_gll<P1><<<dim3(bpe, (n_orb + opc - 1) / opc), dim3(P2, E), smem, c->stream>>>(g, c->d_tab, psi, c->n_int,
                                                                                    n_orb, opc, ev);
   ApplyArgs a{psi, c->n_int, out, c->n_int, n_orb, nullptr, 0, nullptr, 0, 0, nullptr, 0, nullptr, 0, 0};
-  k_assemble<double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, P1, ev, a);
+  k_assemble<P1, double><<<dim3(assemble_blocks(c, n_orb), n_orb), 128, 0, c->stream>>>(g, ev, a);
   k_diag_add<<<608, 256, 0, c->stream>>>(c->n_int, n_orb, vn, psi, out);
   c->n_launch += 3;
   TDKS_CU(c, cudaGetLastError());
