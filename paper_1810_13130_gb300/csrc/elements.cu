@@ -193,6 +193,149 @@ __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const
   }
 }
 
+// Split form of the element body for the double-float contractions: Hbar is real, so
+// the real and imaginary parts pass through the element one after the other.  Each
+// thread then holds real lines only, which halves the line registers and the shared
+// memory per element: the double-float kernel fits in 128 registers (no spills up to
+// p = 6, 8-56 bytes at p = 7, 8 against 190-540 in the complex form; 9 % faster at p = 6).  FP32 (no gain measured) and FP64
+// (bound by the FP64 pipe) keep the complex lines.
+template <int P1, typename T, class OrbFn>
+__device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB, const T* sBT, const T* sK,
+                                                     const T* sw, T* S1, T* S2, double* red,
+                                               const double* __restrict__ vks, long long eidx,
+                                               int o_begin, int o_end, OrbFn orb,
+                                               Cx<T>* __restrict__ ev, double* part,
+                                               int64_t part_stride, long long pslot) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  typedef Cx<T> V;
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
+  int ex = 0, ey = 0, ez = 0;
+  const bool valid = plain_elem(g, eidx, ex, ey, ez);
+  const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  T fx = from_d<T>(0.0), fy = from_d<T>(0.0), fz = from_d<T>(0.0);
+  T vx[P1];
+#pragma unroll
+  for (int q = 0; q < P1; ++q) vx[q] = from_d<T>(0.0);
+  if (valid) {
+    const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
+    const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
+    const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
+    const double J = 0.125 * hx * hy * hz;
+    const double wl = to_d(sw[u]) * to_d(sw[v]);
+    fx = from_d<T>(hy * hz / (4.0 * hx) * wl);
+    fy = from_d<T>(hx * hz / (4.0 * hy) * wl);
+    fz = from_d<T>(hx * hy / (4.0 * hz) * wl);
+    const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
+    const double* vp = vks + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
+#pragma unroll
+    for (int q = 0; q < P1; ++q) vx[q] = from_d<T>(vp[q] * J * wl * to_d(sw[q]));
+  }
+  const long long plane = (long long)g.nix * g.niy;
+  // gather: z-column (a = u, b = v); Loewdin scales of the column (once per CTA)
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  constexpr bool kDF = std::is_same<T, Df>::value;
+  const int Ig = ex * g.p + u, Jg = ey * g.p + v;
+  const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
+  const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
+  T gsc[P1];
+#pragma unroll
+  for (int c = 0; c < P1; ++c) {
+    const int K = ez * g.p + c;
+    gsc[c] = from_d<T>((inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0);
+  }
+
+  for (int o = o_begin; o < o_end; ++o) {
+    const double2* in = nullptr;
+    double sc = 1.0;
+    if (!orb(o, in, sc)) continue;
+    T scT;
+    if constexpr (kF32) scT = d2f_bits(sc);
+    else scT = from_d<T>(sc);
+    T apt = from_d<T>(0.0);
+    T* evr = reinterpret_cast<T*>(ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1);
+#pragma unroll 1
+    for (int comp = 0; comp < 2; ++comp) {   // real part, then imaginary part
+      T col[P1], t[P1];
+#pragma unroll
+      for (int c = 0; c < P1; ++c) {
+        const int K = ez * g.p + c;
+        vzero(col[c]);
+        if (inG && K >= 1 && K <= g.niz) {
+          const double2 w2 = in[baseG + plane * (K - 1)];
+          const double x = comp ? w2.y : w2.x;
+          if constexpr (kF32) {
+            col[c] = d2f_bits(x) * (gsc[c] * scT);
+          } else {
+            col[c] = df_mul(d2df_bits(x), df_mul(gsc[c], scT));
+          }
+        }
+      }
+      // forward z, y, x
+      cs_apply<P1>(sB, col, t);
+      store_line(t, S1 + v * P1 + u, P2);
+      __syncthreads();
+      load_line(col, S1 + v * P2 + u, P1);
+      cs_apply<P1>(sB, col, t);
+      store_line(t, S2 + v * P2 + u, P1);
+      __syncthreads();
+      T uq[P1];
+      load_line(col, S2 + v * P2 + u * P1, 1);
+      cs_apply<P1>(sB, col, uq);
+      store_line(uq, S1 + v * P2 + u * P1, 1);          // U (Gauss-point values)
+      cs_apply<P1>(sK, uq, t);
+#pragma unroll
+      for (int q = 0; q < P1; ++q) {
+        T r = vscale(vx[q], uq[q]);
+        madd(r, fx, t[q]);
+        t[q] = r;
+      }
+      store_line(t, S2 + v * P2 + u * P1, 1);           // R
+      __syncthreads();
+      load_line(col, S1 + v * P2 + u, P1);
+      cs_apply<P1>(sK, col, t);
+#pragma unroll
+      for (int q = 0; q < P1; ++q) {
+        T r = S2[v * P2 + q * P1 + u];
+        madd(r, fy, t[q]);
+        S2[v * P2 + q * P1 + u] = r;
+      }
+      __syncthreads();
+      load_line(col, S1 + v * P1 + u, P2);
+      cs_apply<P1>(sK, col, t);
+#pragma unroll
+      for (int q = 0; q < P1; ++q) {
+        T r = S2[q * P2 + v * P1 + u];
+        madd(r, fz, t[q]);
+        uq[q] = r;
+        dot_acc(apt, col[q], r);
+      }
+      __syncthreads();
+      // backward z, y, x
+      cs_apply<P1>(sBT, uq, t);
+      store_line(t, S1 + v * P1 + u, P2);
+      __syncthreads();
+      load_line(col, S1 + v * P2 + u, P1);
+      cs_apply<P1>(sBT, col, t);
+      store_line(t, S2 + v * P2 + u, P1);
+      __syncthreads();
+      load_line(col, S2 + v * P2 + u * P1, 1);
+      cs_apply<P1>(sBT, col, t);
+      if (valid) {
+#pragma unroll
+        for (int a2 = 0; a2 < P1; ++a2) evr[2 * a2 + comp] = t[a2];
+      }
+      __syncthreads();
+    }
+    if (part) {
+      double apart;
+      if constexpr (kF32) apart = f2d_bits(apt);
+      else apart = f2d_bits(apt.hi) + f2d_bits(apt.lo);
+      const double s = block_sum(apart, red);
+      if (threadIdx.x + blockDim.x * threadIdx.y == 0) part[(long long)o * part_stride + pslot] = s;
+    }
+  }
+}
+
 // Register budget of the element kernels: at most 128 registers, so that two CTAs
 // (16 warps) share an SM.
 template <int P1, typename T>
@@ -228,6 +371,42 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
     return true;
   };
   hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
+                        a.part_stride, blockIdx.x);
+}
+
+// double-float: split element body (real lines, no register spills at two CTAs per SM)
+template <int P1, typename T>
+__global__ void __launch_bounds__(256, 2) k_hbar_split(Geom g, const T* __restrict__ tab,
+                                              const double* __restrict__ vks, ApplyArgs a,
+                                              int orb_per_cta, Cx<T>* __restrict__ ev) {
+  constexpr int P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  T* sB = reinterpret_cast<T*>(smem);
+  T* sBT = sB + CS;
+  T* sK = sBT + CS;
+  T* sw = sK + CS;
+  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
+  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  T* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  __syncthreads();
+  const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const int o0 = blockIdx.y * orb_per_cta;
+  const int o1 = min(o0 + orb_per_cta, a.n_orb);
+  auto orb = [&](int o, const double2*& in, double& sc) -> bool {
+    if (a.kry) {
+      if (a.kry[o].status != KRY_ACTIVE) return false;
+      sc = a.kry[o].s[a.kj];
+    }
+    in = a.in_base + (long long)o * a.in_stride;
+    return true;
+  };
+  hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
                         a.part_stride, blockIdx.x);
 }
 
@@ -580,6 +759,63 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ 
       return true;
     };
     hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
+                          static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk);
+  }
+}
+
+template <int P1, typename T>
+__global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restrict__ sys,
+                                                    const BItem* __restrict__ items, int n_items,
+                                                    const T* __restrict__ tab, int* __restrict__ qctr) {
+  constexpr int P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  T* sB = reinterpret_cast<T*>(smem);
+  T* sBT = sB + CS;
+  T* sK = sBT + CS;
+  T* sw = sK + CS;
+  const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
+  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  T* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
+  __syncthreads();
+  // the current item's system descriptor is staged in shared memory: its fields are
+  // re-read where used instead of occupying registers across the element body
+  // items are taken from a shared ticket counter (zeroed before every launch), so
+  // CTAs that draw items of finished orbitals move on at once and the grid stays
+  // balanced whatever the mix of active orbitals
+  __shared__ BSys sS;
+  __shared__ BItem sW;
+  __shared__ int sIt;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      const int it = atomicAdd(qctr, 1);
+      sIt = it;
+      if (it < n_items) sW = items[it];
+    }
+    __syncthreads();
+    if (sIt >= n_items) break;
+    for (int i = tid; i < (int)(sizeof(BSys) / 8); i += nthr)
+      reinterpret_cast<long long*>(&sS)[i] = reinterpret_cast<const long long*>(&sys[sW.sys])[i];
+    __syncthreads();
+    const BItem w = sW;
+    const BSys& S = sS;
+    const Geom& g = S.g;
+    const long long eidx = (long long)w.eblk * blockDim.y + threadIdx.y;
+    auto orb = [&](int o, const double2*& in, double& sc) -> bool {
+      const KryOrb& K = S.kry[o];
+      if (K.status != KRY_ACTIVE) return false;
+      const int j = K.k;
+      in = bvec(S, K, o, j);
+      sc = K.s[j];
+      return true;
+    };
+    hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                           static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk);
   }
 }
@@ -1079,8 +1315,14 @@ template <int P1, typename T>
 tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
-  TDKS_CU(c, set_smem(k_hbar<P1, T>, smem));
+  constexpr bool kSplit = std::is_same<T, Df>::value;
+  constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);   // shared-memory entry per point
+  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  if constexpr (kSplit) {
+    TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  } else {
+    TDKS_CU(c, set_smem(k_hbar<P1, T>, smem));
+  }
   const size_t need = (size_t)a.n_orb * c->n_elem * P3 * sizeof(Cx<T>);
   if (need > c->evec_bytes) {
     cudaFree(c->d_evec);
@@ -1103,7 +1345,10 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
                                                  : (const T*)c->d_tabdf;
   const Geom g = tdks_geom(c);
   if (c->kb) TDKS_TRY(kb_project(c, a));
-  k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
+  if constexpr (kSplit)
+    k_hbar_split<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
+  else
+    k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
   if (a.lanczos && a.kry && a.part) {
     k_alpha<<<a.n_orb, 256, 0, c->stream>>>(a.kry, a.part, a.part_stride, bpe, a.kj);
     if (c->kb) TDKS_TRY(kb_alpha(c, a));
@@ -1316,7 +1561,8 @@ template <int P1, typename T>
 static size_t hbar_batch_smem_t(int E) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<T>);
+  constexpr size_t line = std::is_same<T, Df>::value ? sizeof(T) : sizeof(Cx<T>);
+  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
 }
 
 template <int P1>
@@ -1344,14 +1590,16 @@ template <int P1, typename T>
 static cudaError_t hbar_batch_launch_t(const BSys* sys, const BItem* items, int n_items, int E,
                                        int grid, const void* tab, int* qctr, cudaStream_t st, int* occ) {
   const size_t smem = hbar_batch_smem_t<P1, T>(E);
+  // split body for double-float (see k_hbar_split), complex body otherwise
+  void (*kern)(const BSys*, const BItem*, int, const T*, int*);
+  if constexpr (std::is_same<T, Df>::value) kern = k_hbar_batch_split<P1, T>;
+  else kern = k_hbar_batch<P1, T>;
   // the kernel also holds ~330 B of static shared memory: opt in for any large size
-  cudaError_t e = cudaFuncSetAttribute(k_hbar_batch<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_hbar_batch<P1, T>, Cfg<P1>::P2 * E, smem);
+  if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, Cfg<P1>::P2 * E, smem);
   if (n_items <= 0) return cudaSuccess;
-  k_hbar_batch<P1, T><<<grid, dim3(Cfg<P1>::P2, E), smem, st>>>(sys, items, n_items,
-                                                               static_cast<const T*>(tab), qctr);
+  kern<<<grid, dim3(Cfg<P1>::P2, E), smem, st>>>(sys, items, n_items, static_cast<const T*>(tab), qctr);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,12 @@ __device__ __forceinline__ Cx<Df> vscale(Df c, const Cx<Df>& v) {
   return Cx<Df>{df_mul(c, v.re), df_mul(c, v.im)};
 }
 
+// real double-float lines (the split form of the element kernel)
+__device__ __forceinline__ Df vadd(const Df& a, const Df& b) { return df_add(a, b); }
+__device__ __forceinline__ Df vsub(const Df& a, const Df& b) { return df_sub(a, b); }
+__device__ __forceinline__ void madd(Df& acc, Df c, const Df& v) { df_madd(acc, c, v); }
+__device__ __forceinline__ Df vscale(Df c, const Df& v) { return df_mul(c, v); }
+
 // scalar conversions used in set-up code (not in the inner loops)
 template <typename T>
 __device__ __forceinline__ T from_d(double x) { return (T)x; }
@@ -123,6 +129,9 @@ __device__ __forceinline__ void dot_acc(Df& acc, const Cx<Df>& a, const Cx<Df>& 
 }
 template <typename T>
 __device__ __forceinline__ Cx<T> vscale(T c, const Cx<T>& v) { return Cx<T>{c * v.re, c * v.im}; }
+// acc += a b (real lines)
+__device__ __forceinline__ void dot_acc(float& acc, const float& a, const float& b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void dot_acc(Df& acc, const Df& a, const Df& b) { df_madd(acc, a, b); }
 
 // out = M in for a centrosymmetric N x N matrix M stored folded (layout in
 // tdks_internal.h): pairs (i, N-1-i) of the input are combined into even and odd
@@ -233,6 +242,16 @@ __device__ __forceinline__ void cs_apply_df1(const Df* __restrict__ t, const Df 
 #pragma unroll
     for (int i = 0; i < h; ++i) dfa_madd(c, Mr[i], e[i]);
     out[h] = df_norm(c.hi, c.err);
+  }
+}
+
+// real double-float line
+template <int N>
+__device__ __forceinline__ void cs_apply(const Df* __restrict__ t, const Df (&in)[N], Df (&out)[N]) {
+  if constexpr (N == 1) {
+    out[0] = df_mul(t[0], in[0]);
+  } else {
+    cs_apply_df1<N>(t, in, out);
   }
 }
 
