@@ -501,13 +501,15 @@ __device__ __forceinline__ double assemble_rows(const Geom& g, const Cx<T>* __re
       double re = 0.0, im = 0.0;
       float fre = 0.f, fim = 0.f;
       Df dre{0.f, 0.f}, dim{0.f, 0.f};
-      // fixed trip counts keep base[] and xo[] in registers
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int kx = 0; kx < 2; ++kx) {
-          if (k >= nb || kx >= nxc) continue;
-          const Cx<T> c = evo[base[k] + xo[kx]];
+      // exactly nb * nxc additions in the fixed order (z, y, then x); the offsets are
+      // picked by selects so that base[] and xo[] stay in registers (an unrolled loop
+      // with predicates would turn into 16 unconditional FP64 additions per node)
+      const int ncon = nb * nxc;
+      for (int tcon = 0; tcon < ncon; ++tcon) {
+          const int k = nxc == 2 ? (tcon >> 1) : tcon;
+          const long long bk = k == 0 ? base[0] : (k == 1 ? base[1] : (k == 2 ? base[2] : base[3]));
+          const long long xk = (nxc == 2 && (tcon & 1)) ? xo[1] : xo[0];
+          const Cx<T> c = evo[bk + xk];
           if constexpr (kF32) {
             fre += c.re;
             fim += c.im;

@@ -91,6 +91,26 @@ def test_apply_H_molecule_workload_sampled_rows():
     assert abs(lhs - rhs) < 1e-11 * abs(Ha).max().item()
 
 
+def test_apply_H_graded_workload_sampled_rows():
+    """Graded 24^3 mesh, p = 8, 5 orbitals (the all-electron-like workload, 6.97 M DoF):
+    sampled outputs of the FP64 and double-float contractions against the oracle."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.config3()
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    psi = synth.random_psi(cfg.n_orb, m.N_int, seed=11)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=12).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    g = _cuda(psi)
+    got = ctx.apply_H(g).cpu().numpy()
+    got_df = ctx.apply_H(g, prec=tdks.DF64).cpu().numpy()
+    rng = np.random.default_rng(13)
+    rows = np.concatenate([rng.choice(m.N_int, 30, replace=False), [0, m.N_int - 1, m.N_int // 2]])
+    ref = ham.apply_H_rows(m, v, psi, rows)
+    assert _rel(got[:, rows], ref) < 1e-12
+    assert _rel(got_df[:, rows], ref) < 1e-11
+
+
 def test_apply_H_fp32_error_vs_fp64_oracle():
     cfg = synth.small_config(3, 3, 2, p=6, n_orb=2)
     m = Mesh.from_config(cfg)
