@@ -1338,9 +1338,10 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   }
   Cx<T>* ev = static_cast<Cx<T>*>(c->d_evec);
   const int bpe = elem_blocks_t<P1>(c);
-  // orbitals per CTA: V and geometry are reused across them; keep >= 4 CTAs per SM
+  // orbitals per CTA: V and geometry are reused across them; keep >= 8 CTAs per SM
+  // (about four waves at two CTAs per SM, so the last partial wave costs little)
   int opc = 1;
-  while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
+  while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 8 * 152) opc *= 2;
   const int ochunks = (a.n_orb + opc - 1) / opc;
   const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab
                  : std::is_same<T, float>::value ? (const T*)c->d_tabf
@@ -1674,7 +1675,7 @@ static tdks_status hbar_gll_t(tdks_ctx* c, const double2* psi, const double* vn,
   Cx<double>* ev = static_cast<Cx<double>*>(c->d_evec);
   const int bpe = elem_blocks_t<P1>(c);
   int opc = 1;
-  while (opc < n_orb && (long long)bpe * ((n_orb + 2 * opc - 1) / (2 * opc)) >= 4 * 152) opc *= 2;
+  while (opc < n_orb && (long long)bpe * ((n_orb + 2 * opc - 1) / (2 * opc)) >= 8 * 152) opc *= 2;
   const Geom g = tdks_geom(c);
   k_hbar_gll<P1><<<dim3(bpe, (n_orb + opc - 1) / opc), dim3(P2, E), smem, c->stream>>>(g, c->d_tab, psi, c->n_int,
                                                                                    n_orb, opc, ev);
