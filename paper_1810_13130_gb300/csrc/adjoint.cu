@@ -45,6 +45,7 @@ __global__ void k_combine_basis(long long n, double2* out, const double2* V0, co
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int j = 0; j < m; ++j) {
       const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
       const double2 cj = c[j];

@@ -347,6 +347,7 @@ __global__ void k_kry_recomb(long long n, double2* out, int64_t so, const double
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int j = 0; j < m; ++j) {
       const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
       re = fma(cr[j], v.x, fma(-ci[j], v.y, re));
@@ -480,6 +481,7 @@ __global__ void k_brecomb(const BSys* __restrict__ sys, const BRow* __restrict__
   const long long i1 = min(n, (w.rblk + 1) * chunk);
   for (long long i = w.rblk * chunk + threadIdx.x; i < i1; i += blockDim.x) {
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int j = 0; j < m; ++j) {
       const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
       re = fma(cr[j], v.x, fma(-ci[j], v.y, re));
