@@ -223,6 +223,20 @@ def profile_traffic(prec: str):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def replica_throughput(units_local: float, t_local: float, dist=None, device: str = "cpu"):
+    """Whole-job throughput of N replicas (one workload per rank, no data exchange):
+    the units of all ranks over the slowest rank's time.  Returns (value, t_max).
+    With dist=None (one process) it is units / t."""
+    if dist is None:
+        return units_local / t_local, t_local
+    import torch
+    world = dist.get_world_size()
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t = tt.item()
+    return world * units_local / t, t
+
+
 def _run_steps(tdks, torch, cfg, prec, steps, warmup, local_rank, psi0, dist=None, timing=True):
     """K timed Magnus steps of a fresh context from psi0 (kicked on the device)."""
     ctx = tdks.Context.from_config(cfg)
@@ -297,13 +311,9 @@ def ours(args, rank: int, world: int, local_rank: int):
                                  cfg.n_orb, seed=1)
     ctx, psi, t, stats, cnt, clocks = _run_steps(tdks, torch, cfg, prec, args.steps, args.warmup,
                                                  local_rank, psi0, dist)
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
     n_int = ctx.n_int
     applies = sum(s["applies"] for s in stats)
-    value = world * cfg.n_orb * args.steps / t
+    value, t = replica_throughput(cfg.n_orb * args.steps, t, dist, "cuda")
     hpsi = world * n_int * applies / t / 1e9
     # roofline of the dominant kernel (the Hbar element kernel, timed inside the region)
     P1 = cfg.p + 1
