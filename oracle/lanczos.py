@@ -9,7 +9,9 @@ Sec. VI.B, Eqs. 36-38.  For each orbital separately:
                                             projected -i tau Hbar has modulus |tau| beta_j;
                                             tau < 0 gives the backward propagator)
     stop when eps_j <= tol:  z = ||psibar|| Q_j y;  otherwise q_{j+1} = w / beta_j.
-The plain three-term recurrence is used (the paper names no re-orthogonalization).
+The plain three-term recurrence is the default (the paper names no
+re-orthogonalization); full re-orthogonalization by classical Gram-Schmidt applied
+twice is an option.
 
 The paper sets no cap on the Krylov dimension.  With a cap k_max, an unconverged
 basis is used for the largest sub-step tau' = tau_rem / 2^m (m = 1, 2, ...) whose
@@ -38,12 +40,15 @@ def exp_tridiag_e1(alpha, beta_off, tau):
 
 
 def expm_lanczos(apply_vec, psi: np.ndarray, tau: float, tol: float, k_max: int = 64,
-                 max_sub: int = 1000, k_fixed=None):
+                 max_sub: int = 1000, k_fixed=None, reorth: bool = False):
     """Return (exp(-i tau Hbar) psi, info).  psi: (n_orb, N) complex.
 
     info["k"][a] lists the Krylov dimension of every sub-step of orbital a.
     k_fixed (int or per-orbital sequence) forces the dimension of a single step
-    (used to replay another implementation's stopping index)."""
+    (used to replay another implementation's stopping index).
+    reorth: after the three-term update, w is orthogonalized against every basis
+    vector so far by classical Gram-Schmidt applied twice (CGS2); alpha_j keeps its
+    three-term value and beta_j = ||w|| is taken after the two passes."""
     psi = np.atleast_2d(psi)
     out = np.empty_like(psi, dtype=complex)
     info = {"k": [], "err": []}
@@ -69,6 +74,10 @@ def expm_lanczos(apply_vec, psi: np.ndarray, tau: float, tol: float, k_max: int 
                 w = w - a_j * Q[j]
                 if j > 0:
                     w = w - beta[j - 1] * Q[j - 1]
+                if reorth:
+                    Qm = np.array(Q)                     # (j+1, N)
+                    for _ in range(2):
+                        w = w - Qm.T @ (Qm.conj() @ w)
                 b_j = float(np.linalg.norm(w))
                 alpha.append(a_j)
                 beta.append(b_j)

@@ -88,3 +88,41 @@ def test_k_fixed_replays_adaptive_choice():
     ks = [k[0] for k in info["k"]]
     out2, info2 = expm_lanczos(f, psi, 0.4, 1e-10, 64, k_fixed=ks)
     np.testing.assert_array_equal(out, out2)
+
+
+def test_reorthogonalized_lanczos_keeps_the_basis_orthonormal_and_matches_expm():
+    """CGS2 re-orthogonalization: same exponential, orthonormal basis to rounding even
+    where the three-term recurrence loses orthogonality (long run, wide spectrum)."""
+    import scipy.linalg
+    from oracle.lanczos import expm_lanczos
+    rng = np.random.default_rng(4)
+    n = 300
+    lam = np.concatenate([np.linspace(0, 1, n - 5), [40, 60, 80, 120, 200]])
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    H = (U * lam) @ U.conj().T
+    psi = (rng.standard_normal((1, n)) + 1j * rng.standard_normal((1, n)))
+    psi /= np.linalg.norm(psi)
+    ref = scipy.linalg.expm(-1j * 0.2 * H) @ psi[0]
+    out, _ = expm_lanczos(lambda x: H @ x, psi, 0.2, 1e-12, 120, reorth=True)
+    assert np.abs(out[0] - ref).max() < 1e-10
+
+    def basis(reorth, k=60):
+        q = psi[0] / np.linalg.norm(psi[0])
+        Q, beta = [q], 0.0
+        prev = np.zeros_like(q)
+        for j in range(k):
+            w = H @ Q[j]
+            a = np.vdot(Q[j], w).real
+            w = w - a * Q[j] - beta * prev
+            if reorth:
+                Qm = np.array(Q)
+                for _ in range(2):
+                    w = w - Qm.T @ (Qm.conj() @ w)
+            beta = np.linalg.norm(w)
+            prev = Q[j]
+            Q.append(w / beta)
+        Qm = np.array(Q)
+        return np.abs(Qm.conj() @ Qm.T - np.eye(len(Q))).max()
+
+    assert basis(True) < 1e-13
+    assert basis(False) > 1e-6      # the plain recurrence drifts on this spectrum
