@@ -354,6 +354,15 @@ tdks_status tdks_batch_phase_ms(tdks_batch* b, double ms[5], int passes[2]);
 tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]);
 const char* tdks_batch_last_error(const tdks_batch* b);
 
+/* Lanczos variant of every exponential of the context (tdks_expm, the Magnus steps,
+ * the adjoint).  reorth = 0 (default): the plain three-term recurrence (Sec. VI.B
+ * names no re-orthogonalization).  reorth = 1: after the three-term update the new
+ * vector is orthogonalized against every basis vector so far by classical
+ * Gram-Schmidt applied twice (CGS2), and beta_j is its norm after the two passes;
+ * alpha_j keeps its three-term value.  Costs about 4 (j + 1) vector reads at step j.
+ * The batched engine does not take this option. */
+tdks_status tdks_set_lanczos(tdks_ctx* ctx, int reorth);
+
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar
  * colour launches, element-orbital applications, and -- when timing is on --
  * the summed device time of the Hbar applications inside tdks_expm measured

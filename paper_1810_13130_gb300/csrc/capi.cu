@@ -60,6 +60,10 @@ tdks_status upload(tdks_ctx* c, T** p, const std::vector<T>& h) {
 
 void free_ctx(tdks_ctx* c) {
   kb_free(c);
+  if (c) {
+    cudaFree(c->d_ro_part);
+    cudaFree(c->d_ro_h);
+  }
   if (!c) return;
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->d_brk[d]);
@@ -492,6 +496,12 @@ tdks_status tdks_propagate_host(tdks_ctx* c, const double* psi_in, double* psi_o
   }
   TDKS_CU(c, cudaMemcpyAsync(psi_out, c->d_psi_e2e, vb, cudaMemcpyDeviceToHost, c->stream));
   TDKS_CU(c, cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_lanczos(tdks_ctx* c, int reorth) {
+  if (!c || (reorth != 0 && reorth != 1)) return TDKS_ERR_ARG;
+  c->lanczos_reorth = reorth;
   return TDKS_OK;
 }
 

@@ -375,6 +375,91 @@ __global__ void k_kry_after(KryOrb* kry, int n_orb) {
   }
 }
 
+// ---- optional re-orthogonalization (classical Gram-Schmidt, two passes) --------
+// After the three-term update has written w = V_{j+1}, w -= sum_i q_i (q_i^H w) over
+// i = 0..j, twice; q_i = s_i V_i.  Partial dots per (chunk, i, orbital), summed in a
+// fixed order; then ||w||^2 is recomputed for beta_j.
+constexpr int kRoChunks = 128;
+
+__global__ void k_ro_dot(long long n, const double2* V0, int64_t s0, const double2* VW, int64_t wsorb,
+                         int j, const KryOrb* kry, double2* part) {
+  __shared__ double red[2][kThreads / 32];
+  const int o = blockIdx.z, i = blockIdx.y;
+  const KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  const double2* q = (i == 0) ? V0 + (long long)o * s0 : VW + (long long)o * wsorb + (long long)(i - 1) * n;
+  const double2* w = VW + (long long)o * wsorb + (long long)j * n;
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long e1 = min(n, (blockIdx.x + 1) * chunk);
+  double re = 0.0, im = 0.0;
+  for (long long e = blockIdx.x * chunk + threadIdx.x; e < e1; e += blockDim.x) {
+    const double2 a = q[e], x = w[e];
+    re = fma(a.x, x.x, fma(a.y, x.y, re));
+    im = fma(a.x, x.y, fma(-a.y, x.x, im));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, off);
+    im += __shfl_down_sync(0xffffffffu, im, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = re;
+    red[1][threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) {
+      sr += red[0][k];
+      si += red[1][k];
+    }
+    const double sc = K.s[i];
+    part[((long long)o * TDKS_KMAX + i) * gridDim.x + blockIdx.x] = make_double2(sc * sr, sc * si);
+  }
+}
+
+// h[o][i] = sum of the chunk partials (ascending), one warp per (i, orbital)
+__global__ void k_ro_fin(const KryOrb* kry, const double2* part, int nch, double2* h) {
+  const int o = blockIdx.y, i = blockIdx.x;
+  if (kry[o].status != KRY_ACTIVE) return;
+  if (threadIdx.x == 0) {
+    double sr = 0.0, si = 0.0;
+    const double2* p = part + ((long long)o * TDKS_KMAX + i) * nch;
+    for (int k = 0; k < nch; ++k) {
+      sr += p[k].x;
+      si += p[k].y;
+    }
+    h[(long long)o * TDKS_KMAX + i] = make_double2(sr, si);
+  }
+}
+
+// w -= sum_i h_i s_i V_i
+__global__ void k_ro_update(long long n, const double2* V0, int64_t s0, double2* VW, int64_t wsorb, int j,
+                            const KryOrb* kry, const double2* h) {
+  __shared__ double hr[TDKS_KMAX], hi[TDKS_KMAX];
+  const int o = blockIdx.y;
+  const KryOrb& K = kry[o];
+  if (K.status != KRY_ACTIVE) return;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double2 v = h[(long long)o * TDKS_KMAX + i];
+    hr[i] = v.x * K.s[i];
+    hi[i] = v.y * K.s[i];
+  }
+  __syncthreads();
+  const double2* v0 = V0 + (long long)o * s0;
+  const double2* vw = VW + (long long)o * wsorb;
+  double2* w = VW + (long long)o * wsorb + (long long)j * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double2 x = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 q = (i == 0) ? v0[e] : vw[(long long)(i - 1) * n + e];
+      x.x -= hr[i] * q.x - hi[i] * q.y;
+      x.y -= hr[i] * q.y + hi[i] * q.x;
+    }
+    w[e] = x;
+  }
+}
+
 // ---- batched exponential: per-orbital state machine over many systems --------
 // RESTART -> (norm) ACTIVE -> (apply, decide) ACTIVE | CONVERGED | SUBSTEP | FAILED;
 // CONVERGED/SUBSTEP -> (recombine) DONE | RESTART.  One pass of the loop body
@@ -595,6 +680,16 @@ static tdks_status ensure_krylov(tdks_ctx* c, int w, int n_orb, int kmax) {
   return TDKS_OK;
 }
 
+static tdks_status ensure_reorth(tdks_ctx* c) {
+  if (c->d_ro_part) return TDKS_OK;
+  if (cudaMalloc(&c->d_ro_part, (size_t)c->n_orb * TDKS_KMAX * kRoChunks * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&c->d_ro_h, (size_t)c->n_orb * TDKS_KMAX * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    return tdks_fail(c, TDKS_ERR_NOMEM, "re-orthogonalization buffers");
+  }
+  return TDKS_OK;
+}
+
 struct KrySummary {
   int k, status, k_total, nsub, applies, kseen;
 };
@@ -649,6 +744,7 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
     c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
     for (int j = 0; j < kmax; ++j) {
+      const double2* Vj0 = cur;   // V_0 of this sub-step (re-orthogonalization)
       const double2* Vj = (j == 0) ? cur : VW + (int64_t)(j - 1) * n;
       const int64_t sj = (j == 0) ? n : wsorb;
       const double2* Vm = (j == 1) ? cur : (j >= 2 ? VW + (int64_t)(j - 2) * n : nullptr);
@@ -660,8 +756,22 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
       TDKS_TRY(launch_hbar_apply(c, a, prec));
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
       c->n_apply_units += (int64_t)n_active * c->n_elem;
-      k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm, kb_norm_parts(c),
-                                             kb_norm_blocks(c));
+      if (c->lanczos_reorth) {
+        TDKS_TRY(ensure_reorth(c));
+        for (int pass = 0; pass < 2; ++pass) {
+          k_ro_dot<<<dim3(kRoChunks, j + 1, n_orb), kThreads, 0, c->stream>>>(n, Vj0, n, VW, wsorb, j, kry,
+                                                                              c->d_ro_part);
+          k_ro_fin<<<dim3(j + 1, n_orb), 32, 0, c->stream>>>(kry, c->d_ro_part, kRoChunks, c->d_ro_h);
+          k_ro_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, Vj0, n, VW, wsorb, j, kry, c->d_ro_h);
+        }
+        // ||w||^2 after the passes (the assembly's and the nonlocal partials are stale)
+        k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(VW + (int64_t)j * n, wsorb, n, kry, npart, ps);
+        k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nb, nullptr, 0);
+        c->n_launch += 8;
+      } else {
+        k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm, kb_norm_parts(c),
+                                               kb_norm_blocks(c));
+      }
       c->n_launch += 1;
       TDKS_CU(c, cudaGetLastError());
       TDKS_TRY(read_summary(c, kry, n_orb, h.data()));

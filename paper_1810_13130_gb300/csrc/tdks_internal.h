@@ -110,6 +110,9 @@ struct tdks_ctx {
   bool propagation_ready = false;
   void* adj = nullptr;          // objective / adjoint state (adjoint.cu)
   void* kb = nullptr;           // nonlocal Kleinman-Bylander projectors (kb.cu)
+  int lanczos_reorth = 0;       // 1: CGS2 re-orthogonalization of every new Lanczos vector
+  double2* d_ro_part = nullptr; // its partial dots [n_orb][TDKS_KMAX][chunks]
+  double2* d_ro_h = nullptr;    // its projections [n_orb][TDKS_KMAX]
   // counters
   int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0;
   double apply_ms = 0.0;

@@ -96,6 +96,7 @@ def lib():
         "tdks_objective_forward": [v, p, i, i, d, _dp, _dp, _dp, i, d, i, i, _dp, _dp],
         "tdks_objective_backward": [v, i, _dp],
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
+        "tdks_set_lanczos": [v, i],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
         "tdks_apply_H_gll": [v, p, p, p, i],
         "tdks_nuclear_potential_nodes": [v, p],
@@ -134,7 +135,7 @@ def exported_symbols() -> list:
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
-                        "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info",
+                        "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
                         "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
                         "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
@@ -233,6 +234,9 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(lib().tdks_set_timing(self.h, int(bool(on))), "tdks_set_timing")
+
+    def set_lanczos(self, reorth: bool):
+        self._check(lib().tdks_set_lanczos(self.h, int(bool(reorth))), "tdks_set_lanczos")
 
     def get_counters(self, reset: bool = False) -> dict:
         c = Counters()

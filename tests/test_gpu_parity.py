@@ -203,6 +203,26 @@ def test_expm_matches_oracle(tau, kmax):
         assert max(len(ks) for ks in info["k"]) > 1      # sub-steps were exercised
 
 
+@pytest.mark.parametrize("tau,kmax", [(0.3, 64), (0.5, 6)])
+def test_expm_with_reorthogonalization_matches_oracle(tau, kmax):
+    """CGS2 re-orthogonalized Lanczos (tdks_set_lanczos) against the oracle's, including
+    sub-steps; and against the plain recurrence (same exponential within tolerance)."""
+    cfg = synth.small_config(3, 2, 2, p=4, n_orb=3)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=23).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    psi = synth.random_psi(3, m.N_int, seed=24) * np.array([[1.0], [0.5], [2.0]])
+    ctx.set_lanczos(True)
+    out, k = ctx.expm(_cuda(psi), tau, tol=1e-10, k_max=kmax)
+    ref, info = expm_lanczos(lambda x: ham.apply_H(m, v, x), psi, tau, 1e-10, kmax, reorth=True)
+    assert k == [sum(ks) for ks in info["k"]]
+    assert _rel(out.cpu().numpy(), ref) < 1e-10
+    ctx.set_lanczos(False)
+    plain, _ = ctx.expm(_cuda(psi), tau, tol=1e-10, k_max=kmax)
+    assert _rel(out.cpu().numpy(), plain.cpu().numpy()) < 1e-9
+
+
 def test_expm_edge_cases():
     from paper_1810_13130_gb300 import tdks
     cfg = synth.small_config(2, 2, 2, p=2, n_orb=2)
