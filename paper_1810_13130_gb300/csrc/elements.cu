@@ -197,15 +197,18 @@ __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const
 // the real and imaginary parts pass through the element one after the other.  Each
 // thread then holds real lines only, which halves the line registers and the shared
 // memory per element: the double-float kernel fits in 128 registers (no spills up to
-// p = 6, 8-56 bytes at p = 7, 8 against 190-540 in the complex form; 9 % faster at p = 6).  FP32 (no gain measured) and FP64
-// (bound by the FP64 pipe) keep the complex lines.
+// p = 6, 8-56 bytes at p = 7, 8 against 190-540 in the complex form; 9 % faster at p = 6).
+// The next orbital's input columns are prefetched into shared memory during the
+// imaginary pass (7 % faster at p = 6: the loads no longer stall the two CTAs of an SM).
+// FP32 (no gain measured) and FP64 (bound by the FP64 pipe) keep the complex lines.
 template <int P1, typename T, class OrbFn>
 __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB, const T* sBT, const T* sK,
                                                      const T* sw, T* S1, T* S2, double* red,
                                                const double* __restrict__ vks, long long eidx,
                                                int o_begin, int o_end, OrbFn orb,
                                                Cx<T>* __restrict__ ev, double* part,
-                                               int64_t part_stride, long long pslot) {
+                                               int64_t part_stride, long long pslot,
+                                                     double2* __restrict__ pfbuf) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   typedef Cx<T> V;
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
@@ -244,15 +247,41 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
     gsc[c] = from_d<T>((inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0);
   }
 
-  for (int o = o_begin; o < o_end; ++o) {
+  // The z-columns of the next active orbital are copied into shared memory
+  // (cp.async, 16 B per node, zero-filled outside the interior) while the current
+  // orbital is computed; the buffer holds P1 double2 per thread, [c][thread].
+  const int tid_pf = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr_pf = blockDim.x * blockDim.y;
+  auto issue = [&](const double2* src_base) {
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      const int K = ez * g.p + c;
+      const bool ok = inG && K >= 1 && K <= g.niz;
+      const double2* src = ok ? src_base + baseG + plane * (K - 1) : src_base;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(pfbuf + c * nthr_pf + tid_pf);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 16 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int o = o_begin;
+  {
+    const double2* in0 = nullptr;
+    double sc0 = 1.0;
+    while (o < o_end && !orb(o, in0, sc0)) ++o;
+    if (o < o_end) issue(in0);
+  }
+  while (o < o_end) {
     const double2* in = nullptr;
     double sc = 1.0;
-    if (!orb(o, in, sc)) continue;
+    orb(o, in, sc);
+    int on = o_end;   // next active orbital, found when its prefetch is issued
     T scT;
     if constexpr (kF32) scT = d2f_bits(sc);
     else scT = from_d<T>(sc);
     T apt = from_d<T>(0.0);
     T* evr = reinterpret_cast<T*>(ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll 1
     for (int comp = 0; comp < 2; ++comp) {   // real part, then imaginary part
       T col[P1], t[P1];
@@ -261,7 +290,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
         const int K = ez * g.p + c;
         vzero(col[c]);
         if (inG && K >= 1 && K <= g.niz) {
-          const double2 w2 = in[baseG + plane * (K - 1)];
+          const double2 w2 = pfbuf[c * nthr_pf + tid_pf];
           const double x = comp ? w2.y : w2.x;
           if constexpr (kF32) {
             col[c] = d2f_bits(x) * (gsc[c] * scT);
@@ -274,6 +303,14 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
       cs_apply<P1>(sB, col, t);
       store_line(t, S1 + v * P1 + u, P2);
       __syncthreads();
+      // the buffer was last read before this barrier: refill it for the next orbital
+      if (comp == 1) {
+        const double2* in_n = nullptr;
+        double sc_n = 1.0;
+        on = o + 1;
+        while (on < o_end && !orb(on, in_n, sc_n)) ++on;
+        if (on < o_end) issue(in_n);
+      }
       load_line(col, S1 + v * P2 + u, P1);
       cs_apply<P1>(sB, col, t);
       store_line(t, S2 + v * P2 + u, P1);
@@ -333,6 +370,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
       const double s = block_sum(apart, red);
       if (threadIdx.x + blockDim.x * threadIdx.y == 0) part[(long long)o * part_stride + pslot] = s;
     }
+    o = on;
   }
 }
 
@@ -407,7 +445,8 @@ __global__ void __launch_bounds__(256, 2) k_hbar_split(Geom g, const T* __restri
     return true;
   };
   hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
-                        a.part_stride, blockIdx.x);
+                              a.part_stride, blockIdx.x,
+                              reinterpret_cast<double2*>(smem + off + (size_t)blockDim.y * 2 * P3 * sizeof(T)));
 }
 
 // alpha_j = sum of the element partials (fixed order), for the active orbitals
@@ -818,7 +857,8 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restr
       return true;
     };
     hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
-                          static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk);
+                                static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk,
+                                reinterpret_cast<double2*>(smem + off + (size_t)blockDim.y * 2 * P3 * sizeof(T)));
   }
 }
 
@@ -1319,7 +1359,8 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   constexpr bool kSplit = std::is_same<T, Df>::value;
   constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);   // shared-memory entry per point
-  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line +
+                      (kSplit ? (size_t)E * P2 * P1 * sizeof(double2) : 0);   // + prefetch buffer
   if constexpr (kSplit) {
     TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   } else {
@@ -1564,8 +1605,10 @@ template <int P1, typename T>
 static size_t hbar_batch_smem_t(int E) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  constexpr size_t line = std::is_same<T, Df>::value ? sizeof(T) : sizeof(Cx<T>);
-  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  constexpr bool kSplit = std::is_same<T, Df>::value;
+  constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);
+  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line +
+         (kSplit ? (size_t)E * Cfg<P1>::P2 * P1 * sizeof(double2) : 0);   // + prefetch buffer
 }
 
 template <int P1>
