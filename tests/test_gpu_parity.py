@@ -223,6 +223,28 @@ def test_expm_with_reorthogonalization_matches_oracle(tau, kmax):
     assert _rel(out.cpu().numpy(), plain.cpu().numpy()) < 1e-9
 
 
+def test_expm_df64_two_orbitals_per_cta_with_uneven_convergence():
+    """Double-float Lanczos on a mesh large enough that each element-kernel CTA runs two
+    orbitals (3072 elements, p = 6: 615 CTAs per orbital pair), with smooth and rough
+    orbitals that leave the recurrence at different j: the CTA skips the converged
+    orbital and prefetches the next active one.  Against the FP64 path, which equals
+    the oracle on the small systems above."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(16, 16, 12, p=6, n_orb=4, L=16.0)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=25).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    smooth = synth.smooth_orbitals(tuple(m.Ni), 2, seed=26)
+    rough = synth.random_psi(2, m.N_int, seed=27)
+    psi = np.stack([smooth[0], rough[0], smooth[1], rough[1]])
+    out64, k64 = ctx.expm(_cuda(psi), 0.1, tol=1e-10, k_max=64)
+    outdf, kdf = ctx.expm(_cuda(psi), 0.1, tol=1e-10, k_max=64, prec=tdks.DF64)
+    assert min(k64[0], k64[2]) < max(k64[1], k64[3])   # the smooth orbitals leave first
+    assert _rel(outdf.cpu().numpy(), out64.cpu().numpy()) < 1e-10
+    assert max(abs(a - b) for a, b in zip(kdf, k64)) <= 1
+
+
 def test_expm_edge_cases():
     from paper_1810_13130_gb300 import tdks
     cfg = synth.small_config(2, 2, 2, p=2, n_orb=2)
