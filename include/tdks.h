@@ -59,8 +59,14 @@ typedef enum {
 typedef enum {
   TDKS_FP64 = 0,   /* double contractions                                  */
   TDKS_FP32 = 1,   /* float contractions with float accumulation, FP64 I/O  */
-  TDKS_DF64 = 2    /* double-float (compensated float-pair) contractions:
+  TDKS_DF64 = 2,   /* double-float (compensated float-pair) contractions:
                       ~48-bit accurate products and sums on the FP32 pipe   */
+  TDKS_BF16 = 3    /* accuracy study: every contraction operand (input, 1-D
+                      operator coefficients, each contraction result feeding
+                      the next) rounded to bfloat16, FP32 products and sums,
+                      i.e. the arithmetic of a BF16 tensor-core contraction,
+                      run on the CUDA cores (no speed claim).  Single-system
+                      calls only: tdks_batch_create rejects it.             */
 } tdks_prec;
 
 typedef enum {

@@ -76,6 +76,7 @@ void free_ctx(tdks_ctx* c) {
   cudaFree(c->d_tab);
   cudaFree(c->d_tabf);
   cudaFree(c->d_tabdf);
+  cudaFree(c->d_tabbf);
   cudaFree(c->d_occ);
   cudaFree(c->d_R);
   cudaFree(c->d_Z);
@@ -115,7 +116,16 @@ void free_ctx(tdks_ctx* c) {
   delete c;
 }
 
-// V_HXC = V_H[rho] + V_XC[rho] of the orbitals psi; rho left in c->d_rho.
+// float -> nearest bfloat16 (ties to even), returned as a float; finite inputs only
+float round_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
 // Folded storage of a centrosymmetric n x n matrix (layout in tdks_internal.h).
 void fold_centrosymmetric(const double* M, int n, double* out) {
   const int h = n / 2;
@@ -139,6 +149,7 @@ tdks_status check_orb(tdks_ctx* c, int n_orb) {
 
 }  // namespace
 
+// V_HXC = V_H[rho] + V_XC[rho] of the orbitals psi; rho left in c->d_rho.
 tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters) {
   const size_t nf = (size_t)(c->n_elem * c->nq3);
   TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
@@ -313,6 +324,9 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
   if ((st = upload(c, &c->d_tabdf, tabdf)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_tab, tab)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_tabf, tabf)) != TDKS_OK) return fail(st);
+  std::vector<float> tabbf(tab.size());
+  for (size_t k = 0; k < tab.size(); ++k) tabbf[k] = round_bf16(tabf[k]);
+  if ((st = upload(c, &c->d_tabbf, tabbf)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_occ, c->occ)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_R, c->R)) != TDKS_OK) return fail(st);
   if ((st = upload(c, &c->d_Z, c->Z)) != TDKS_OK) return fail(st);
@@ -394,7 +408,7 @@ tdks_status tdks_nuclear_potential(tdks_ctx* c, double* v) {
 tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb, int prec) {
   if (!c || !psi || !out) return TDKS_ERR_ARG;
   if (n_orb < 1) return tdks_fail(c, TDKS_ERR_ARG, "n_orb >= 1");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
     return tdks_fail(c, TDKS_ERR_ARG, "precision");
   ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0,
               0, nullptr, 0, nullptr, 0, 0};
@@ -440,7 +454,7 @@ tdks_status tdks_expm(tdks_ctx* c, const double* in, double* out, int n_orb, dou
   if (!c || !in || !out) return TDKS_ERR_ARG;
   TDKS_TRY(check_orb(c, n_orb));
   if (!(tol > 0) || !std::isfinite(tau)) return tdks_fail(c, TDKS_ERR_ARG, "tol > 0, finite tau");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
     return tdks_fail(c, TDKS_ERR_ARG, "precision");
   if (in != out)
     TDKS_CU(c, cudaMemcpyAsync(out, in, (size_t)n_orb * c->n_int * sizeof(double2),
@@ -535,7 +549,7 @@ tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, co
   TDKS_TRY(check_orb(c, n_orb));
   if (!c->propagation_ready) return tdks_fail(c, TDKS_ERR_ARG, "call tdks_init_propagation first");
   if (!(dt > 0) || !(tol > 0)) return tdks_fail(c, TDKS_ERR_ARG, "dt > 0 and tol > 0");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64)
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
     return tdks_fail(c, TDKS_ERR_ARG, "precision");
   const size_t vb = (size_t)n_orb * c->n_int * sizeof(double2);
   const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);

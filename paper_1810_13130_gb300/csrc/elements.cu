@@ -21,6 +21,8 @@
 // Assembly: elements are processed in 8 parity colours (one launch each); two
 // elements of one colour never share a node, so the scatter is a plain
 // read-modify-write and the summation order is fixed (deterministic results).
+#include <cuda_bf16.h>
+
 #include <cstdio>
 #include <type_traits>
 
@@ -53,7 +55,26 @@ struct Cfg {
 // [o_begin, o_end) that orb(o, in, sc) accepts (in: the orbital's input vector,
 // sc: its scale); results go to ev, alpha partials to part[o][pslot].
 // Shared tables (sB, sBT, sK, sw) must be loaded and synchronized by the caller.
-template <int P1, typename T, class OrbFn>
+// BF16-operand mode (kBF, T = float): every value that enters a contraction as an
+// operand -- the gathered input, the 1-D operator coefficients (rounded in the
+// table) and each contraction result that feeds the next contraction -- is rounded
+// to bfloat16; products and sums stay FP32.  That is the arithmetic of a BF16
+// tensor-core contraction with FP32 accumulation, run on the CUDA cores to measure
+// its accuracy.
+template <bool kBF, int N>
+__device__ __forceinline__ void bf_round(Cx<float> (&v)[N]) {
+  if constexpr (kBF) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      v[i].re = __bfloat162float(__float2bfloat16_rn(v[i].re));
+      v[i].im = __bfloat162float(__float2bfloat16_rn(v[i].im));
+    }
+  }
+}
+template <bool kBF, int N, typename V>
+__device__ __forceinline__ void bf_round(V (&)[N]) {}
+
+template <int P1, typename T, class OrbFn, bool kBF = false>
 __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const T* sBT, const T* sK,
                                                const T* sw, Cx<T>* S1, Cx<T>* S2, double* red,
                                                const double* __restrict__ vks, long long eidx,
@@ -128,16 +149,20 @@ __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const
       }
     }
     // forward z, y, x
+    bf_round<kBF>(col);
     cs_apply<P1>(sB, col, t);
+    bf_round<kBF>(t);
     store_line(t, S1 + v * P1 + u, P2);
     __syncthreads();
     load_line(col, S1 + v * P2 + u, P1);
     cs_apply<P1>(sB, col, t);
+    bf_round<kBF>(t);
     store_line(t, S2 + v * P2 + u, P1);
     __syncthreads();
     V uq[P1];
     load_line(col, S2 + v * P2 + u * P1, 1);
     cs_apply<P1>(sB, col, uq);
+    bf_round<kBF>(uq);
     store_line(uq, S1 + v * P2 + u * P1, 1);          // U (Gauss-point values)
     cs_apply<P1>(sK, uq, t);
 #pragma unroll
@@ -175,11 +200,14 @@ __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const
     else apart = apt;
     __syncthreads();
     // backward z, y, x
+    bf_round<kBF>(uq);
     cs_apply<P1>(sBT, uq, t);
+    bf_round<kBF>(t);
     store_line(t, S1 + v * P1 + u, P2);
     __syncthreads();
     load_line(col, S1 + v * P2 + u, P1);
     cs_apply<P1>(sBT, col, t);
+    bf_round<kBF>(t);
     store_line(t, S2 + v * P2 + u, P1);
     __syncthreads();
     load_line(col, S2 + v * P2 + u * P1, 1);
@@ -376,7 +404,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
 
 // Register budget of the element kernels: at most 128 registers, so that two CTAs
 // (16 warps) share an SM.
-template <int P1, typename T>
+template <int P1, typename T, bool kBF = false>
 __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
                                               int orb_per_cta, Cx<T>* __restrict__ ev) {
@@ -408,8 +436,8 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
     in = a.in_base + (long long)o * a.in_stride;
     return true;
   };
-  hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
-                        a.part_stride, blockIdx.x);
+  hbar_elem_body<P1, T, decltype(orb), kBF>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev,
+                                            a.part, a.part_stride, blockIdx.x);
 }
 
 // double-float: split element body (real lines, no register spills at two CTAs per SM)
@@ -1353,7 +1381,7 @@ int elem_blocks_t(const tdks_ctx* c) {
   return (int)((c->n_elem + Cfg<P1>::E - 1) / Cfg<P1>::E);
 }
 
-template <int P1, typename T>
+template <int P1, typename T, bool kBF = false>
 tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
@@ -1364,7 +1392,7 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   if constexpr (kSplit) {
     TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   } else {
-    TDKS_CU(c, set_smem(k_hbar<P1, T>, smem));
+    TDKS_CU(c, set_smem(k_hbar<P1, T, kBF>, smem));
   }
   const size_t need = (size_t)a.n_orb * c->n_elem * P3 * sizeof(Cx<T>);
   if (need > c->evec_bytes) {
@@ -1385,14 +1413,14 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 8 * 152) opc *= 2;
   const int ochunks = (a.n_orb + opc - 1) / opc;
   const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab
-                 : std::is_same<T, float>::value ? (const T*)c->d_tabf
+                 : std::is_same<T, float>::value ? (const T*)(kBF ? c->d_tabbf : c->d_tabf)
                                                  : (const T*)c->d_tabdf;
   const Geom g = tdks_geom(c);
   if (c->kb) TDKS_TRY(kb_project(c, a));
   if constexpr (kSplit)
     k_hbar_split<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
   else
-    k_hbar<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
+    k_hbar<P1, T, kBF><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
   if (a.lanczos && a.kry && a.part) {
     k_alpha<<<a.n_orb, 256, 0, c->stream>>>(a.kry, a.part, a.part_stride, bpe, a.kj);
     if (c->kb) TDKS_TRY(kb_alpha(c, a));
@@ -1557,6 +1585,8 @@ int assemble_blocks(const tdks_ctx* c, int n_orb) {
 tdks_status launch_hbar_apply(tdks_ctx* c, const ApplyArgs& a, int prec) {
   if (prec == TDKS_FP32) {
     TDKS_DISPATCH(c->P1, (hbar_t<P1, float>(c, a)));
+  } else if (prec == TDKS_BF16) {
+    TDKS_DISPATCH(c->P1, (hbar_t<P1, float, true>(c, a)));
   } else if (prec == TDKS_DF64) {
     TDKS_DISPATCH(c->P1, (hbar_t<P1, Df>(c, a)));
   } else {

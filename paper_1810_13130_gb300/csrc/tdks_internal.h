@@ -78,6 +78,7 @@ struct tdks_ctx {
   double* d_tab = nullptr;     // double tables (layout in tables.cpp)
   float* d_tabf = nullptr;     // float copy
   float* d_tabdf = nullptr;    // double-float copy (hi, lo pairs)
+  float* d_tabbf = nullptr;    // float copy rounded to bfloat16 (BF16-operand mode)
   double* d_occ = nullptr;
   double* d_R = nullptr;
   double* d_Z = nullptr;

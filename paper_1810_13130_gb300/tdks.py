@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdks.so")
 
-FP64, FP32, DF64 = 0, 1, 2
+FP64, FP32, DF64, BF16 = 0, 1, 2, 3
 PRECOND_FDM, PRECOND_JACOBI = 0, 1
 NUC_KIND = {"none": 0, "soft": 1, "erf": 2, "bare": 3, "harmonic": 4}
 _dp = C.POINTER(C.c_double)

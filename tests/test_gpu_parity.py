@@ -124,6 +124,23 @@ def test_apply_H_fp32_error_vs_fp64_oracle():
     assert 1e-9 < err < 1e-5
 
 
+def test_apply_H_bf16_operand_error_vs_fp64_oracle():
+    """BF16-operand mode (bfloat16 operands, FP32 products and sums): an error at the
+    bfloat16 level (8-bit significand, ~4e-3 per rounding), far above FP32's."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(3, 3, 2, p=6, n_orb=2)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    psi = synth.random_psi(2, m.N_int, seed=10)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=11).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    ref = ham.apply_H(m, v, psi)
+    e16 = _rel(ctx.apply_H(_cuda(psi), prec=tdks.BF16).cpu().numpy(), ref)
+    e32 = _rel(ctx.apply_H(_cuda(psi), prec=tdks.FP32).cpu().numpy(), ref)
+    assert 1e-4 < e16 < 5e-2
+    assert e16 > 100 * e32
+
+
 @pytest.mark.parametrize("p,n", [(3, (3, 2, 2)), (6, (3, 2, 2)), (8, (2, 2, 1))])
 def test_apply_H_df64_matches_fp64_oracle(p, n):
     """Double-float contractions: FP64-level agreement (~48-bit arithmetic)."""
