@@ -323,6 +323,34 @@ def test_magnus_steps_atom_workload_df64():
         assert _rel(g.cpu().numpy(), ref) < 1e-10
 
 
+def test_magnus_step_molecule_workload_properties():
+    """One predictor-corrector step of the molecule workload (857,375 DoF, 16 orbitals) in
+    the launch configuration the benchmark times, checked by properties that hold at any
+    size: the kicked orbitals stay orthonormal (the exponential is unitary up to the Krylov
+    tolerance), the reported dipole is that of the new density, and the DF64 step gives
+    the FP64 orbitals."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.config2()
+    m = Mesh.from_config(cfg)
+    psi0 = synth.smooth_orbitals(tuple(m.Ni), cfg.n_orb, seed=1)
+    out = {}
+    for prec in (tdks.FP64, tdks.DF64):
+        ctx = _ctx(cfg)
+        g = _cuda(psi0)
+        ctx.kick(g, cfg.kick, cfg.kick_dir)
+        ctx.init_propagation(g)
+        st = ctx.magnus_step(g, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=prec)
+        d = ctx.dipole(ctx.density(g))
+        out[prec] = (g.cpu().numpy(), st, d)
+        ctx.close()
+    psi, st, d = out[tdks.FP64]
+    gram = psi.conj() @ psi.T
+    assert np.abs(gram - np.eye(cfg.n_orb)).max() < 1e-9
+    assert st["k_full_max"] >= st["k_half_max"] > 1 and st["substeps"] == 0
+    np.testing.assert_allclose(st["dipole"], d, rtol=1e-12, atol=1e-14)
+    assert _rel(out[tdks.DF64][0], psi) < 1e-10
+
+
 def test_magnus_step_with_field_small_system():
     cfg = synth.small_config(3, 2, 2, p=3, n_orb=2)
     m = Mesh.from_config(cfg)
