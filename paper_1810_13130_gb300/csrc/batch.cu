@@ -233,7 +233,7 @@ tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphCon
   B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
   B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
   B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, s));
-  B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
+  B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, s));
   B_CU(b, launch_bloop_control(h, sys, b->d_orbs, b->n_gorb, iter, kMaxSubPasses * b->kmax,
                                b->d_ctrl + 2, b->d_qctr, kDegStreams, s));
   return TDKS_OK;
@@ -305,7 +305,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   B_TRY(b, fork_fields(b), "fork");
   for (int s = 0; s < b->n_sys; ++s) {
     tdks_ctx* c = b->ctx[s];
-    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err)),
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err, b->prec)),
           "corrector");
     B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr,
                                           zero)), "corrector");
@@ -323,7 +323,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
     tdks_ctx* c = b->ctx[s];
     const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
     B_CU(b, cudaMemcpyAsync(c->d_vhxc2, c->d_vhxc1, fb, cudaMemcpyDeviceToDevice, c->stream));
-    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err)), "history");
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err, b->prec)), "history");
     B_TRY(b, ctx_try(b, c, dipole_graph(c, c->d_rho, b->d_dip + 3 * (size_t)s, b->d_ctrl + 3,
                                         3 * (int64_t)b->n_sys)), "dipole");
   }
@@ -774,7 +774,7 @@ tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]) {
     B_CU(b, cudaEventRecord(ev[4], b->st));
     B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->st));
     B_CU(b, cudaEventRecord(ev[5], b->st));
-    B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
+    B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, b->st));
     B_CU(b, cudaEventRecord(ev[6], b->st));
     B_CU(b, cudaEventSynchronize(ev[6]));
     for (int i = 0; i < 6; ++i) {

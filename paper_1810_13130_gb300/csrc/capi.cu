@@ -150,9 +150,9 @@ tdks_status check_orb(tdks_ctx* c, int n_orb) {
 }  // namespace
 
 // V_HXC = V_H[rho] + V_XC[rho] of the orbitals psi; rho left in c->d_rho.
-tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters) {
+tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters, int prec) {
   const size_t nf = (size_t)(c->n_elem * c->nq3);
-  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
+  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec));
   if (c->hartree) {
     TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters));
   } else {
@@ -170,9 +170,10 @@ tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int
 
 
 // vhxc_of for stream capture (fixed-length Poisson CG, no host reads)
-tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter, int* err) {
+tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter, int* err,
+                       int prec) {
   const size_t nf = (size_t)(c->n_elem * c->nq3);
-  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho));
+  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec));
   if (c->hartree) {
     TDKS_TRY(hartree_graph(c, c->d_rho, c->d_vh, n_iter, err));
   } else {
@@ -570,7 +571,7 @@ tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, co
   st.applies += app;
   st.substeps += nsub;
   // corrector: V(t + dt/2) from the density of psi^{n-1/2}
-  TDKS_TRY(vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[0]));
+  TDKS_TRY(vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[0], prec));
   // d_vtmp now holds V_HXC(t + dt/2) (vhxc_of used d_vtmp as scratch before writing it)
   TDKS_TRY(launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr, Eh));
   if (keep_vmid) TDKS_CU(c, cudaMemcpyAsync(keep_vmid, c->d_vks, fb, cudaMemcpyDeviceToDevice, c->stream));
@@ -580,7 +581,7 @@ tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, co
   st.substeps += nsub;
   // history: V_HXC^{n-2} <- V_HXC^{n-1}, V_HXC^{n-1} <- V_HXC[rho(psi^n)]
   std::swap(c->d_vhxc1, c->d_vhxc2);
-  TDKS_TRY(vhxc_of(c, psi, n_orb, c->d_vhxc1, &st.cg_iters[1]));
+  TDKS_TRY(vhxc_of(c, psi, n_orb, c->d_vhxc1, &st.cg_iters[1], prec));
   TDKS_TRY(run_dipole(c, c->d_rho, st.dipole));
   if (stats) *stats = st;
   return TDKS_OK;

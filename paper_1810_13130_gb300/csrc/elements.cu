@@ -1221,6 +1221,78 @@ __global__ void __launch_bounds__(256) k_density(Geom g, const double* __restric
   }
 }
 
+// Density in the double-float runs: the interpolation to the Gauss points is a
+// cell-level contraction and runs in double-float (real, then imaginary part, as
+// in the split element kernel); |psi_q|^2 is formed in double-float, rounded once
+// to FP64 and accumulated over the orbitals in FP64.
+template <int P1>
+__global__ void __launch_bounds__(256) k_density_df(Geom g, const Df* __restrict__ tab,
+                                                    const double2* __restrict__ psi, int64_t stride,
+                                                    int n_orb, const double* __restrict__ occ,
+                                                    double* __restrict__ rho) {
+  constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Df* sB = reinterpret_cast<Df*>(smem);
+  const size_t off = (CS * sizeof(Df) + 15) & ~size_t(15);
+  Df* S1 = reinterpret_cast<Df*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
+  Df* S2 = S1 + P3;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int i = tid; i < CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
+  const int u = threadIdx.x % P1, v = threadIdx.x / P1;
+  int ex = 0, ey = 0, ez = 0;
+  const bool valid = plain_elem(g, (long long)blockIdx.x * blockDim.y + threadIdx.y, ex, ey, ez);
+  __syncthreads();
+  const int I = ex * g.p + u, Jn = ey * g.p + v;
+  const bool inIJ = valid && I >= 1 && I <= g.nix && Jn >= 1 && Jn <= g.niy;
+  const long long base = inIJ ? (long long)(I - 1) + (long long)g.nix * (Jn - 1) : 0;
+  const long long plane = (long long)g.nix * g.niy;
+  Df gsc[P1];   // Loewdin scales of this thread's z-column
+#pragma unroll
+  for (int c = 0; c < P1; ++c) {
+    const int K = ez * g.p + c;
+    gsc[c] = from_d<Df>((inIJ && K >= 1 && K <= g.niz) ? g.s[0][I] * g.s[1][Jn] * g.s[2][K] : 0.0);
+  }
+  double acc[P1];
+#pragma unroll
+  for (int q = 0; q < P1; ++q) acc[q] = 0.0;
+  for (int o = 0; o < n_orb; ++o) {
+    const double2* in = psi + (long long)o * stride;
+    Df ur[P1];
+#pragma unroll 1
+    for (int comp = 0; comp < 2; ++comp) {
+      Df col[P1], uq[P1];
+#pragma unroll
+      for (int c = 0; c < P1; ++c) {
+        const int K = ez * g.p + c;
+        col[c] = Df{0.f, 0.f};
+        if (inIJ && K >= 1 && K <= g.niz) {
+          const double2 w2 = in[base + plane * (K - 1)];
+          col[c] = df_mul(d2df_bits(comp ? w2.y : w2.x), gsc[c]);
+        }
+      }
+      forward_lines<P1, Df, Df>(col, uq, S1, S2, sB, u, v);
+      if (comp == 0) {
+#pragma unroll
+        for (int q = 0; q < P1; ++q) ur[q] = uq[q];
+      } else {
+        const double f = occ[o];
+#pragma unroll
+        for (int q = 0; q < P1; ++q) {
+          const Df m2 = df_add(df_mul(ur[q], ur[q]), df_mul(uq[q], uq[q]));
+          acc[q] = fma(f, f2d_bits(m2.hi) + f2d_bits(m2.lo), acc[q]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (valid) {
+    const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
+    store_line(acc, rho + e * P3 + v * P2 + u * P1, 1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Density adjoint: element-local (B^T)^(x)3 [2 occ_a g_rho psi_a(x_q)] for every
 // orbital (the assembly and the Loewdin scale follow in k_assemble).
@@ -1478,14 +1550,21 @@ tdks_status interp_t(tdks_ctx* c, const double* nodal, double* fq, double scale,
 }
 
 template <int P1>
-tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho) {
+tdks_status density_t(tdks_ctx* c, const double2* psi, int n_orb, double* rho, int prec) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  const size_t smem = ((CS * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
-  TDKS_CU(c, set_smem(k_density<P1>, smem));
   dim3 block(P2, E), grid((unsigned)((c->n_elem + E - 1) / E));
-  k_density<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, psi, c->n_int, n_orb,
-                                                 c->d_occ, rho);
+  if (prec == TDKS_DF64) {
+    const size_t smem = ((CS * sizeof(Df) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Df);
+    TDKS_CU(c, set_smem(k_density_df<P1>, smem));
+    k_density_df<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), (const Df*)c->d_tabdf, psi, c->n_int,
+                                                      n_orb, c->d_occ, rho);
+  } else {
+    const size_t smem = ((CS * sizeof(double) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * sizeof(Cx<double>);
+    TDKS_CU(c, set_smem(k_density<P1>, smem));
+    k_density<P1><<<grid, block, smem, c->stream>>>(tdks_geom(c), c->d_tab, psi, c->n_int, n_orb,
+                                                   c->d_occ, rho);
+  }
   c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
   return TDKS_OK;
@@ -1625,8 +1704,8 @@ tdks_status launch_cross(tdks_ctx* c, const double2* mu, const double2* phi, int
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }
 
-tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q) {
-  TDKS_DISPATCH(c->P1, (density_t<P1>(c, psi, n_orb, rho_q)));
+tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q, int prec) {
+  TDKS_DISPATCH(c->P1, (density_t<P1>(c, psi, n_orb, rho_q, prec)));
   return tdks_fail(c, TDKS_ERR_ARG, "unsupported degree");
 }
 

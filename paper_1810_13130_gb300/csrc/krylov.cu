@@ -28,6 +28,14 @@
 
 namespace {
 
+using tdks::d2df_bits;
+using tdks::Df;
+using tdks::DfAcc;
+using tdks::df_norm;
+using tdks::dfa_madd;
+using tdks::f2d_bits;
+using tdks::from_d;
+
 constexpr int kThreads = 256;
 constexpr int kBlocks = 608;
 constexpr int kBessMax = 3072;
@@ -357,6 +365,59 @@ __global__ void k_kry_recomb(long long n, double2* out, int64_t so, const double
   }
 }
 
+// Double-float recombination (double-float contraction runs): out_i = sum_j c_j V_j[i]
+// with c_j = ||psi|| s_j y_j as double-float pairs and each FP64 vector entry split
+// exactly into a pair on the integer pipe; the sums are carried as unnormalized
+// (hi, err) pairs and rounded once to FP64.  ~2^-48 relative per term, like the
+// double-float contractions, at a fraction of the FP64 pipe's work (4 FP64 FMAs
+// per complex term otherwise).
+struct RecombCoef {
+  Df r, i, ni;   // c_j: real, imaginary, negated imaginary part
+};
+__device__ __forceinline__ RecombCoef recomb_coef(double f, double yr, double yi) {
+  RecombCoef c;
+  c.r = from_d<Df>(f * yr);
+  c.i = from_d<Df>(f * yi);
+  c.ni = Df{-c.i.hi, -c.i.lo};
+  return c;
+}
+__device__ __forceinline__ double2 recomb_df_node(const RecombCoef* __restrict__ cf, int m,
+                                                 const double2* __restrict__ v0,
+                                                 const double2* __restrict__ vw, long long n,
+                                                 long long i) {
+  DfAcc ar{0.f, 0.f}, ai{0.f, 0.f};
+#pragma unroll 2
+  for (int j = 0; j < m; ++j) {
+    const double2 v = (j == 0) ? v0[i] : vw[(long long)(j - 1) * n + i];
+    const Df vx = d2df_bits(v.x), vy = d2df_bits(v.y);
+    const RecombCoef c = cf[j];
+    dfa_madd(ar, c.r, vx);
+    dfa_madd(ar, c.ni, vy);
+    dfa_madd(ai, c.r, vy);
+    dfa_madd(ai, c.i, vx);
+  }
+  const Df r = df_norm(ar.hi, ar.err), s = df_norm(ai.hi, ai.err);
+  return make_double2(f2d_bits(r.hi) + f2d_bits(r.lo), f2d_bits(s.hi) + f2d_bits(s.lo));
+}
+
+__global__ void k_kry_recomb_df(long long n, double2* out, int64_t so, const double2* V0, int64_t s0,
+                                const double2* Vw, int64_t sw, const KryOrb* kry) {
+  __shared__ RecombCoef cf[TDKS_KMAX];
+  const int o = blockIdx.y;
+  const KryOrb& K = kry[o];
+  const int st = K.status;
+  if (st != KRY_CONVERGED && st != KRY_SUBSTEP) return;
+  const int m = K.k;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) cf[j] = recomb_coef(K.nrm * K.s[j], K.yre[j], K.yim[j]);
+  __syncthreads();
+  const double2* v0 = V0 + (long long)o * s0;
+  const double2* vw = Vw + (long long)o * sw;
+  double2* dst = out + (long long)o * so;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = recomb_df_node(cf, m, v0, vw, n, i);
+}
+
 __global__ void k_kry_after(KryOrb* kry, int n_orb) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n_orb) return;
@@ -576,6 +637,26 @@ __global__ void k_brecomb(const BSys* __restrict__ sys, const BRow* __restrict__
   }
 }
 
+__global__ void k_brecomb_df(const BSys* __restrict__ sys, const BRow* __restrict__ rows) {
+  __shared__ RecombCoef cf[TDKS_KMAX];
+  const BRow w = rows[blockIdx.x];
+  const BSys& S = sys[w.sys];
+  const KryOrb& K = S.kry[w.o];
+  const int st = K.status;
+  if (st != KRY_CONVERGED && st != KRY_SUBSTEP) return;
+  const int m = K.k;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) cf[j] = recomb_coef(K.nrm * K.s[j], K.yre[j], K.yim[j]);
+  __syncthreads();
+  const long long n = S.n_int;
+  const double2* v0 = bcur(S, K, w.o);
+  const double2* vw = S.Vw + (long long)w.o * S.kmax * n;
+  double2* dst = S.out + (long long)w.o * n;
+  const long long chunk = (n + S.n_rblk - 1) / S.n_rblk;
+  const long long i1 = min(n, (w.rblk + 1) * chunk);
+  for (long long i = w.rblk * chunk + threadIdx.x; i < i1; i += blockDim.x)
+    dst[i] = recomb_df_node(cf, m, v0, vw, n, i);
+}
+
 __global__ void k_bkry_after(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -784,8 +865,11 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
       for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
       if (!n_active) break;
     }
-    k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb,
-                                                             kmax, kry);
+    if (prec == TDKS_DF64)
+      k_kry_recomb_df<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb, kry);
+    else
+      k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb,
+                                                               kmax, kry);
     k_kry_after<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(kry, n_orb);
     c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
@@ -836,8 +920,9 @@ cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n, double tol
 }
 
 cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n, const BRow* rows, int n_rows,
-                               cudaStream_t st) {
-  k_brecomb<<<n_rows, kThreads, 0, st>>>(sys, rows);
+                               int prec, cudaStream_t st) {
+  if (prec == TDKS_DF64) k_brecomb_df<<<n_rows, kThreads, 0, st>>>(sys, rows);
+  else k_brecomb<<<n_rows, kThreads, 0, st>>>(sys, rows);
   k_bkry_after<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n);
   return cudaGetLastError();
 }

@@ -213,7 +213,10 @@ tdks_status launch_density_adjoint(tdks_ctx* c, const double2* psi, int n_orb, c
 // g_q += coef wJ_q sum_a Im(conj(mu_a(x_q)) phi_a(x_q))
 tdks_status launch_cross(tdks_ctx* c, const double2* mu, const double2* phi, int n_orb, double coef,
                          double* g_q);
-tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q);
+// prec TDKS_DF64: interpolation in double-float, |psi|^2 summed over orbitals in FP64;
+// any other value: FP64 throughout
+tdks_status launch_density(tdks_ctx* c, const double2* psi, int n_orb, double* rho_q,
+                           int prec = TDKS_FP64);
 int hbar_blocks_per_color(const tdks_ctx* c);
 int assemble_blocks(const tdks_ctx* c, int n_orb);   // partial-sum count of the fused update
 int stiff_blocks_per_color(const tdks_ctx* c);
@@ -300,7 +303,7 @@ cudaError_t launch_bkry_prepare(const BSys* sys, const BOrb* orbs, int n_orbs, c
 cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n_orbs, double tol,
                             cudaStream_t st);
 cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
-                               int n_rows, cudaStream_t st);
+                               int n_rows, int prec, cudaStream_t st);
 // the loop kernels also zero the n_q work ticket counters qctr for the next pass
 cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qctr, int n_q,
                                cudaStream_t st);
@@ -310,12 +313,14 @@ cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, 
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
                               unsigned long long* dof_applies, int* kseen, cudaStream_t st);
 // V_HXC of an orbital block (density, Hartree by the polling CG, LDA) into out (capi.cu)
-tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters);
+tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters,
+                    int prec = TDKS_FP64);
 // capturable forms of the per-system field work (no host synchronization)
 tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err);
 tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err);
 tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter,
-                       int* err);
+                       int* err,
+                       int prec = TDKS_FP64);
 tdks_status dipole_graph(tdks_ctx* c, const double* rho, double* base, const int* step,
                          int64_t step_stride);
 cudaError_t launch_counter_add(int* counter, int inc, cudaStream_t st);

@@ -116,7 +116,7 @@ tdks_status tdks_magnus_step_sc(tdks_ctx* c, double* psi_d, int n_orb, double dt
     int64_t app = 0;
     if (s == TDKS_OK)
       s = run_expm(c, psi, c->d_psi_half, n_orb, dt, tol, k_max, prec, nullptr, &kseen, &app, &nsub);
-    if (s == TDKS_OK) s = vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[1]);
+    if (s == TDKS_OK) s = vhxc_of(c, c->d_psi_half, n_orb, c->d_vtmp, &st.cg_iters[1], prec);
     if (s != TDKS_OK) return done(s);
     st.k_full_max = kseen > st.k_full_max ? kseen : st.k_full_max;
     st.applies += app;

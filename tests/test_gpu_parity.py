@@ -309,11 +309,14 @@ def test_magnus_steps_atom_workload():
 
 
 def test_magnus_steps_atom_workload_df64():
+    """Double-float runs: contractions, Krylov recombination and the density
+    interpolation in double-float; recurrence, small exponential, Poisson and the
+    density and dipole sums in FP64."""
     from paper_1810_13130_gb300 import tdks
     cfg, m, psi0 = _atom_initial_state()
     ctx = _ctx(cfg)
     prop = Propagator.from_config(cfg, m)
-    prop.init(psi0)
+    d0 = prop.init(psi0)
     g = _cuda(psi0)
     ctx.init_propagation(g)
     ref = psi0
@@ -321,6 +324,7 @@ def test_magnus_steps_atom_workload_df64():
         ref, dref, info = prop.magnus_step(ref, cfg.dt)
         st = ctx.magnus_step(g, cfg.dt, tol=cfg.tol, k_max=cfg.k_max, prec=tdks.DF64)
         assert _rel(g.cpu().numpy(), ref) < 1e-10
+        assert abs(st["dipole"][2] - dref[2]) < 1e-10 * abs(dref[2] - d0[2]) + 1e-13
 
 
 def test_magnus_step_molecule_workload_properties():
