@@ -151,6 +151,8 @@ def test_batch_rejects_bad_arguments():
     cfgs = synth.small_batch()[:2]
     with pytest.raises(tdks.TDKSError):
         tdks.Batch(cfgs, [0.05, -1.0])
+    with pytest.raises(tdks.TDKSError):
+        tdks.Batch(cfgs, [0.05, 0.1], prec=tdks.BF16)   # accuracy-study mode: single systems only
     b = tdks.Batch(cfgs, [0.05, 0.1])
     with pytest.raises(tdks.TDKSError):
         b.steps(1)                                   # no init yet
