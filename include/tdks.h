@@ -190,6 +190,9 @@ tdks_status tdks_init_propagation(tdks_ctx* ctx, const double* psi_dev, int n_or
  *   V_mid = V_N + V_HXC[rho(psi_half)] - E_half . r
  *   psi <- exp(-i dt Hbar[V_mid]) psi;  V_HXC^n from rho(psi)
  * E_quarter, E_half: host 3-vectors, the field at t_{n-1} + dt/4 and + dt/2.
+ * prec selects the contraction arithmetic of every Hbar application; with
+ * TDKS_DF64 the Krylov recombination and the interpolation of the density to the
+ * Gauss points are double-float as well (sums over orbitals stay FP64).
  * stats (may be NULL) is filled; synchronizes. */
 tdks_status tdks_magnus_step(tdks_ctx* ctx, double* psi_dev, int n_orb, double dt,
                              const double E_quarter[3], const double E_half[3],
