@@ -144,7 +144,9 @@ tdks_status tdks_nuclear_potential(tdks_ctx* ctx, double* v_q_dev);
 /* out = Hbar psi for n_orb orbitals (Eqs. 15, 21): matrix-free, element by
  * element: Loewdin scale and gather, interpolation to the Gauss points, the
  * kinetic form 1/2 int grad N . grad N and the potential form int V N N, and the
- * scatter-add with the Loewdin scale.  psi_dev and out_dev must not overlap. */
+ * scatter-add with the Loewdin scale.  psi_dev and out_dev must not overlap.
+ * n_orb >= 1 vectors of n_int complex values each; the system's orbital count
+ * does not bound it (the element-result buffer grows to fit). */
 tdks_status tdks_apply_H(tdks_ctx* ctx, const double* psi_dev, double* out_dev,
                          int n_orb, int prec);
 

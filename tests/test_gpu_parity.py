@@ -283,6 +283,44 @@ def test_expm_edge_cases():
     np.testing.assert_allclose(out.cpu().numpy(), np.exp(-0.7j * lam[[0, 5]])[:, None] * e, atol=1e-12)
 
 
+@pytest.mark.parametrize("tau,kmax", [(10.0, 128), (0.05, 4), (0.02, 3)])
+def test_expm_at_the_krylov_limits_matches_oracle(tau, kmax):
+    """Krylov spaces beyond the default cap (72 vectors under the largest cap, 128) and
+    tiny caps (3, 4: tens to a hundred sub-steps) against the oracle's Lanczos with the
+    same cap."""
+    cfg = synth.small_config(3, 2, 2, p=4, n_orb=2)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    v = synth.random_potential(m.n_elem * m.nq ** 3, seed=28).reshape(m.n_elem, -1)
+    ctx.set_potential(_cuda(v))
+    psi = synth.random_psi(2, m.N_int, seed=29)
+    out, k = ctx.expm(_cuda(psi), tau, tol=1e-10, k_max=kmax)
+    ref, info = expm_lanczos(lambda x: ham.apply_H(m, v, x), psi, tau, 1e-10, kmax)
+    assert k == [sum(ks) for ks in info["k"]]
+    assert _rel(out.cpu().numpy(), ref) < 1e-10
+    if kmax == 128:
+        assert min(max(ks) for ks in info["k"]) > 64
+    else:
+        assert min(len(ks) for ks in info["k"]) > 20          # many sub-steps
+
+
+def test_bad_orbital_counts_are_rejected():
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(2, 2, 2, p=2, n_orb=2)
+    m = Mesh.from_config(cfg)
+    ctx = _ctx(cfg)
+    three = torch.zeros((3, m.N_int), dtype=torch.complex128, device="cuda")
+    empty = torch.zeros((0, m.N_int), dtype=torch.complex128, device="cuda")
+    # apply_H takes any number of vectors (>= 1); the Krylov calls are bounded by the
+    # system's orbital count
+    assert torch.count_nonzero(ctx.apply_H(three)).item() == 0
+    with pytest.raises(tdks.TDKSError):
+        ctx.apply_H(empty)
+    for psi in (three, empty):
+        with pytest.raises(tdks.TDKSError):
+            ctx.expm(psi, 0.1)
+
+
 def _atom_initial_state():
     cfg = synth.config1()
     import os
