@@ -17,6 +17,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdks.so")
 
+# contraction arithmetic (tdks_prec): FP64; FP32; DF64 double-float (FP64-level,
+# on the FP32 pipe); BF16 = bfloat16 operands with FP32 sums (accuracy study only)
 FP64, FP32, DF64, BF16 = 0, 1, 2, 3
 PRECOND_FDM, PRECOND_JACOBI = 0, 1
 NUC_KIND = {"none": 0, "soft": 1, "erf": 2, "bare": 3, "harmonic": 4}
