@@ -119,6 +119,7 @@ __global__ void k_kry_start(KryOrb* kry, const double* part, int64_t pstride, in
 struct ChebWork {
   double J[kBessMax + 1];
   double a[TDKS_KMAX], b[TDKS_KMAX];
+  double at[TDKS_KMAX], bt[TDKS_KMAX];   // 2 (a - c)/R and 2 b/R
   double v0[TDKS_KMAX], v1[TDKS_KMAX], v2[TDKS_KMAX];
   double yr[TDKS_KMAX], yi[TDKS_KMAX];
   double scal[4];
@@ -171,30 +172,48 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
   const int N = (int)ceil(z + 14.0 * cbrt(z) + 25.0);
   if (N > kBessMax) return false;
   if (lane == 0) {
-    // Miller: b_{n-1} = (2n/z) b_n - b_{n+1} from n = M down to 1
+    // Miller: b_{n-1} = (2n/z) b_n - b_{n+1} from n = M down to 1.  The factor is
+    // n (2/z) with n carried as a double (exact), and the overflow test reads the
+    // exponent bits, so the FP64 pipe sees two instructions per step.
     const int M = N + 20;
-    const double inv_z = 1.0 / z;
-    double bn1 = 0.0, bn = 1e-280, S = (M % 2 == 0) ? 2.0 * bn : 0.0;
-    for (int n = M; n >= 1; --n) {
-      const double bm = (2.0 * n * inv_z) * bn - bn1;
+    const double two_inv_z = 2.0 * (1.0 / z);
+    double bn1 = 0.0, bn = 1e-280, nd = (double)M, Stail = 0.0;
+    for (int n = M; n >= 1; --n, nd -= 1.0) {
+      const double bm = (nd * two_inv_z) * bn - bn1;
       const int idx = n - 1;
       if (idx <= N) W.J[idx] = bm;
-      S += (idx == 0) ? bm : ((idx % 2 == 0) ? 2.0 * bm : 0.0);
+      else if ((idx & 1) == 0) Stail += 2.0 * bm;   // even terms past N enter the sum only
       bn1 = bn;
       bn = bm;
-      if (fabs(bn) > 1e250) {
+      if ((((unsigned long long)__double_as_longlong(bn) >> 52) & 0x7ffull) > 1853ull) {   // |bn| > 2^830
         bn *= 1e-250;
         bn1 *= 1e-250;
-        S *= 1e-250;
+        Stail *= 1e-250;
         for (int k = idx; k <= N && k <= M; ++k) W.J[k] *= 1e-250;
       }
     }
-    const double inv = 1.0 / S;
-    for (int k = 0; k <= N; ++k) W.J[k] *= inv;
+    W.scal[0] = Stail;
   }
   __syncwarp();
+  // normalization J_0 + 2 sum_{k >= 1} J_2k = 1 (the sum in a fixed order), then J_n
+  // for n >= 1 stored doubled: the expansion uses 2 J_n
+  {
+    double sp = 0.0;
+    for (int k = 2 + 2 * lane; k <= N; k += 64) sp += W.J[k];
+    for (int off = 16; off > 0; off >>= 1) sp += __shfl_down_sync(0xffffffffu, sp, off);
+    const double S = W.J[0] + 2.0 * __shfl_sync(0xffffffffu, sp, 0) + W.scal[0];
+    const double inv = 1.0 / S;
+    __syncwarp();
+    for (int k = lane; k <= N; k += 32) W.J[k] *= (k == 0 ? inv : 2.0 * inv);
+  }
   const double invR = 1.0 / R;
-  // v0 = e_1, v1 = S e_1
+  const double two_invR = 2.0 * invR;
+  // scaled tridiagonal of X = (T - c)/R, doubled: the recurrence v_n = 2 X v_{n-1} - v_{n-2}
+  for (int i = lane; i < m; i += 32) {
+    W.at[i] = two_invR * (W.a[i] - c);
+    W.bt[i] = (i < m - 1) ? two_invR * W.b[i] : 0.0;
+  }
+  // v0 = e_1, v1 = X e_1
   for (int i = lane; i < m; i += 32) {
     W.v0[i] = (i == 0) ? 1.0 : 0.0;
     double t = (i == 0) ? (W.a[0] - c) : 0.0;
@@ -206,7 +225,7 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
   for (int r = 0; r < TDKS_KMAX / 32; ++r) {
     const int i = lane + 32 * r;
     accr[r] = (i < m) ? W.J[0] * W.v0[i] : 0.0;
-    acci[r] = (i < m) ? -2.0 * W.J[1] * W.v1[i] : 0.0;
+    acci[r] = (i < m) ? -W.J[1] * W.v1[i] : 0.0;
   }
   double* vp = W.v0;
   double* vc = W.v1;
@@ -215,23 +234,22 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
     for (int r = 0; r < TDKS_KMAX / 32; ++r) {
       const int i = lane + 32 * r;
       if (i < m) {
-        double t = (W.a[i] - c) * vc[i];
-        if (i > 0) t = fma(W.b[i - 1], vc[i - 1], t);
-        if (i < m - 1) t = fma(W.b[i], vc[i + 1], t);
-        vn[i] = fma(2.0 * invR, t, -vp[i]);
+        double t = fma(W.at[i], vc[i], -vp[i]);
+        if (i > 0) t = fma(W.bt[i - 1], vc[i - 1], t);
+        if (i < m - 1) t = fma(W.bt[i], vc[i + 1], t);
+        vn[i] = t;
       }
     }
     __syncwarp();
-    const double cf = 2.0 * W.J[n];
+    // (-i)^n 2 J_n T_n: real part for even n, imaginary for odd, signs by n mod 4
+    const double cf = W.J[n];
     const int ph = n & 3;
+    const double sg = (ph == 0 || ph == 3) ? cf : -cf;
     for (int r = 0; r < TDKS_KMAX / 32; ++r) {
       const int i = lane + 32 * r;
       if (i < m) {
-        const double v = cf * vn[i];
-        if (ph == 0) accr[r] += v;
-        else if (ph == 1) acci[r] -= v;
-        else if (ph == 2) accr[r] -= v;
-        else acci[r] += v;
+        if (ph & 1) acci[r] = fma(sg, vn[i], acci[r]);
+        else accr[r] = fma(sg, vn[i], accr[r]);
       }
     }
     double* t = vp;
