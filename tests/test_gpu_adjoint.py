@@ -63,6 +63,22 @@ def test_adjoint_matches_oracle_small_system(hartree):
     assert torch.equal(psi.cpu(), torch.from_numpy(psi0))
 
 
+def test_adjoint_with_double_float_forward_matches_oracle():
+    """The objective propagated with double-float contractions (recomputed the same way
+    in the backward sweep): J and the gradient against the oracle's FP64 adjoint."""
+    from paper_1810_13130_gb300 import tdks
+    cfg, m, psi0, E, w, e, dt = _small_problem(True)
+    prop = Propagator.from_config(cfg, m, tol=1e-12, k_max=200)
+    J_o, g_o = adjoint.objective_and_gradient(prop, psi0, E, w, e, dt, n_s=12, tol_adj=1e-12)
+    ctx = _ctx(cfg)
+    psi = torch.from_numpy(psi0).cuda()
+    J, _ = ctx.objective_forward(psi, E.reshape(-1, 6), w, e, dt, ckpt_every=2, tol=1e-12,
+                                 k_max=64, prec=tdks.DF64)
+    g = ctx.objective_backward(n_s=12)
+    assert abs(J - J_o) <= 1e-10 * abs(J_o)
+    assert np.abs(g - g_o.reshape(-1, 6)).max() <= 1e-8 * np.abs(g_o).max()
+
+
 def test_adjoint_checkpoint_interval_does_not_change_the_result():
     """Recomputation from a checkpoint replays the forward bit for bit (every kernel
     reduces in a fixed order), so the gradient cannot depend on the interval."""

@@ -77,7 +77,11 @@ def test_expm_with_projectors_matches_oracle():
     assert _rel(out.cpu().numpy(), ref) < 1e-10
 
 
-def test_magnus_steps_with_projectors_match_oracle():
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_magnus_steps_with_projectors_match_oracle(prec):
+    """Local contractions in FP64 or double-float; the projector term is FP64 in both."""
+    from paper_1810_13130_gb300 import tdks
+    pr = {"fp64": tdks.FP64, "df64": tdks.DF64}[prec]
     cfg, m, kb, ctx = _setup(3)
     psi0 = synth.smooth_orbitals(tuple(m.Ni), 2, seed=4)
     prop = Propagator.from_config(cfg, m, nl=kb)
@@ -87,7 +91,7 @@ def test_magnus_steps_with_projectors_match_oracle():
     ref = psi0
     for n in range(3):
         ref, dref, _ = prop.magnus_step(ref, cfg.dt)
-        st = ctx.magnus_step(g, cfg.dt)
+        st = ctx.magnus_step(g, cfg.dt, prec=pr)
         assert _rel(g.cpu().numpy(), ref) < 1e-10
         np.testing.assert_allclose(st["dipole"], dref, rtol=1e-9, atol=1e-12)
 

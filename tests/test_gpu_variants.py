@@ -47,6 +47,30 @@ def test_self_consistent_midpoint_matches_oracle(hartree):
         np.testing.assert_allclose(st["dipole"], dref, rtol=1e-9, atol=1e-12)
 
 
+def test_self_consistent_midpoint_double_float_matches_oracle():
+    """The self-consistent step with double-float contractions: same orbitals as the
+    oracle's FP64 iteration to 1e-10 (the iteration count may differ by one at the
+    sc_tol boundary)."""
+    from paper_1810_13130_gb300 import tdks
+    cfg = synth.small_config(3, 2, 2, p=3, n_orb=2, hartree=True)
+    m = Mesh.from_config(cfg)
+    psi0 = synth.smooth_orbitals(tuple(m.Ni), 2, seed=4)
+    prop = Propagator.from_config(cfg, m, tol=1e-12)
+    prop.init(psi0)
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_cg(1e-13)
+    g = torch.from_numpy(psi0).cuda()
+    ctx.init_propagation(g)
+    ref = psi0
+    for n in range(3):
+        eh = np.array([0.02 * np.sin(n * 0.1 + 0.05), 0.0, 0.01])
+        ref, dref, it = prop.magnus_step_sc(ref, 0.1, eh, sc_tol=1e-11)
+        st = ctx.magnus_step_sc(g, 0.1, eh, tol=1e-12, sc_tol=1e-11, prec=tdks.DF64)
+        assert abs(st["iterations"] - it) <= 1
+        assert _rel(g.cpu().numpy(), ref) < 1e-10
+        np.testing.assert_allclose(st["dipole"], dref, rtol=1e-9, atol=1e-12)
+
+
 def test_self_consistent_midpoint_reports_the_cap():
     from paper_1810_13130_gb300 import tdks
     cfg = synth.small_config(2, 2, 2, p=3, n_orb=1)
