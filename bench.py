@@ -33,6 +33,8 @@ METRIC = ("orbital-steps/s & HΨ GDoF/s, mixed/batched vs FP64 on 1 GB300 at dip
           "err≤1e-6")
 FP64_PEAK_TFLOPS = 1.25          # GB300 dense FP64 (profiling recipe table); probe: 1.256
 FP32_PEAK_TFLOPS = 73.5          # measured FFMA rate of this machine's GB300 (FMA probe)
+WORKLOAD = ("molecule_erf8_16x16x16_p6: [-16,16]^3 bohr, 16^3 hexahedra, p=6, 857,375 DoF, "
+            "16 orbitals, 8 erf atoms, Hartree+LDA, kick 1e-3 x, dt 0.1, Krylov tol 1e-10")
 BF16_NOTE = ("bfloat16 operands with FP32 products and sums, emulated on the CUDA cores to "
              "measure the accuracy of a BF16 tensor-core contraction: the rate is not that of a "
              "tensor-core kernel")
@@ -144,7 +146,7 @@ def reference_arm(args, rank: int):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * 16 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "molecule_erf8_16x16x16_p6 (857,375 DoF, 16 orbitals, dt 0.1)",
+        "config": {"workload": WORKLOAD, "contractions": "fp64", "parallelism": "1 host core",
                    "sample": "one orbital per step"},
         "cpu_baseline": {"value": value, "unit": "orbital-steps/s", "cores": 1, "kind": "oracle",
                          "sample": ORACLE_SAMPLE_DESC, "timed_sample_s": tsum,
@@ -347,9 +349,7 @@ def ours(args, rank: int, world: int, local_rank: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "molecule_erf8_16x16x16_p6: [-16,16]^3 bohr, 16^3 hexahedra, "
-                                   "p=6, 857,375 DoF, 16 orbitals, 8 erf atoms, Hartree+LDA, "
-                                   "kick 1e-3 x, dt 0.1, Krylov tol 1e-10",
+            "config": {"workload": WORKLOAD,
                        "contractions": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "working set > L2 (Krylov basis 14 GB, orbitals 219 MB)"},
             "hpsi_gdofs": hpsi, "applies_per_step": applies / args.steps,
