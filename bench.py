@@ -162,13 +162,13 @@ def reference_arm(args, rank: int):
 # ----------------------------------------------------------------------------
 class ClockSampler:
     def __init__(self, device_index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        self.f = os.fdopen(fd, "w")
         self.dev = device_index
         self.proc = None
 
     def __enter__(self):
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={SMI_FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -178,16 +178,17 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        if self.proc is not None:
+        if self.proc is not None:      # the sampler this object started, by its PID
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-            self.f.close()
+        self.f.close()
 
     def summary(self):
         if self.proc is None:
+            os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         for line in open(self.path):
