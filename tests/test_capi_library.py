@@ -59,3 +59,16 @@ def test_create_rejects_bad_descriptors_without_gpu(libpath):
     m = tdks.MeshDesc(2, 2, 2, Xg.ctypes.data_as(tdks._dp), Xg.ctypes.data_as(tdks._dp),
                       Xg.ctypes.data_as(tdks._dp), 3, 5)          # nq != p+1
     assert L.tdks_create(ctypes.byref(m), ctypes.byref(s), None, ctypes.byref(h)) == -1
+
+
+def test_binding_has_no_cpu_fallback(libpath):
+    """Host tensors are refused before any library call: there is no CPU path."""
+    import numpy as np
+    import torch
+    from paper_1810_13130_gb300 import tdks
+    rho = torch.zeros(8 * 27, dtype=torch.float64)                  # a host tensor
+    b = np.array([0.0, 1.0, 2.0])
+    with pytest.raises(tdks.TDKSError, match="CUDA tensor"):
+        tdks.dipole_noalloc(rho, b, b, b, 2)
+    with pytest.raises(tdks.TDKSError):
+        tdks._dev(torch.zeros(4, dtype=torch.complex64), torch.complex128, "psi")
