@@ -1,6 +1,7 @@
 """Pins for the oracle adjoint: LDA kernel by finite differences, the Frechet
-term against scipy.linalg.expm_frechet, and the full gradient against central
-finite differences of the oracle's own forward propagation."""
+term against scipy.linalg.expm_frechet, dot-product (transpose) tests of the density
+and Hartree/LDA adjoints, and the full gradient against central finite differences
+of the oracle's own forward propagation."""
 import numpy as np
 import pytest
 import scipy.linalg
@@ -69,3 +70,54 @@ def _J(prop, psi0, E, w, e, dt):
         psi, d, _ = prop.magnus_step(psi, dt, E[n, 0], E[n, 1])
         J += w[n + 1] * (e @ d) ** 2
     return J
+
+
+def _dot_mesh():
+    return Mesh(np.linspace(-2.0, 2.0, 4), np.linspace(-1.5, 1.5, 3), np.linspace(-1.0, 1.5, 3), 3)
+
+
+def test_density_adjoint_is_the_transpose_of_the_linearized_density():
+    """Dot-product test: sum_q g_q drho_q = Re <lambda, dpsi> with lambda the density
+    adjoint of g.  rho is quadratic in psi, so its central difference with step 1 is the
+    exact linearization."""
+    m = _dot_mesh()
+    rng = np.random.default_rng(21)
+    occ = np.array([2.0, 1.0])
+    psi = synth.random_psi(2, m.N_int, 22)
+    dpsi = synth.random_psi(2, m.N_int, 23)
+    g = rng.standard_normal((m.n_elem, m.nq ** 3))
+    drho = 0.5 * (ham.density(m, psi + dpsi, occ) - ham.density(m, psi - dpsi, occ))
+    lam = adjoint.density_adjoint(m, psi, g, occ)
+    lhs = np.sum(g * drho)
+    rhs = sum(np.vdot(lam[a], dpsi[a]).real for a in range(2))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_hartree_adjoint_is_the_transpose_of_the_hartree_map():
+    """Dot-product test of the Hartree part of the potential adjoint: V_H is linear in
+    rho, so sum_q g_q V_H[drho]_q = sum_q hxc_adjoint(g)_q drho_q."""
+    from oracle import poisson
+    m = _dot_mesh()
+    rng = np.random.default_rng(24)
+    rho = np.abs(rng.standard_normal((m.n_elem, m.nq ** 3)))
+    drho = rng.standard_normal(rho.shape)
+    g = rng.standard_normal(rho.shape)
+    dvh, _, _ = poisson.hartree(m, drho, None, 1e-14)
+    gr = adjoint.hxc_adjoint(m, rho, g, hartree=True, use_xc=False)
+    lhs, rhs = np.sum(g * dvh), np.sum(gr * drho)
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_xc_adjoint_is_the_linearized_lda_potential():
+    """The LDA part of the potential adjoint against a central difference of v_xc itself."""
+    from oracle import xc
+    m = _dot_mesh()
+    rng = np.random.default_rng(25)
+    rho = rng.uniform(0.01, 2.0, size=(m.n_elem, m.nq ** 3))
+    drho = rng.standard_normal(rho.shape)
+    g = rng.standard_normal(rho.shape)
+    eps = 1e-6
+    dv = (xc.v_xc(rho + eps * drho) - xc.v_xc(rho - eps * drho)) / (2 * eps)
+    gr = adjoint.hxc_adjoint(m, rho, g, hartree=False, use_xc=True)
+    lhs, rhs = np.sum(g * dv), np.sum(gr * drho)
+    assert abs(lhs - rhs) < 1e-7 * max(1.0, abs(lhs))
