@@ -54,8 +54,11 @@ typedef enum {
   TDKS_ERR_NAN = -6             /* a non-finite value reached a reduction     */
 } tdks_status;
 
-/* Arithmetic of the cell-level contractions in apply_H.  Vectors, Lanczos
- * recurrence, small exponential, Poisson, density and dipole are always FP64. */
+/* Arithmetic of the cell-level contractions in apply_H.  Stored vectors, the
+ * Lanczos recurrence, the small exponential, Poisson and the density and dipole
+ * sums are always FP64; with TDKS_DF64 the Krylov recombination (tdks_expm,
+ * tdks_magnus_step) and the density interpolation of a Magnus step are
+ * double-float as well. */
 typedef enum {
   TDKS_FP64 = 0,   /* double contractions                                  */
   TDKS_FP32 = 1,   /* float contractions with float accumulation, FP64 I/O  */
