@@ -394,19 +394,23 @@ tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);
 
 /* Allocation-free dipole (no counterpart in the paper; a service for callers that
  * cannot allocate device memory -- programs whose device memory belongs to another
- * allocator with a fixed budget, or code that must not allocate, or synchronize as
- * cudaMalloc may, once it is running, e.g. a real-time propagation loop).
+ * allocator with a fixed budget, or code that must not allocate once it is running,
+ * e.g. a real-time propagation loop after its start-up).
  * Computes the same int r rho dr as tdks_dipole without a context: rho_q_dev is
- * [nx*ny*nz][(p+1)^3] at the Gauss points (layout as above), X/Y/Z the host
- * breakpoints, 1 <= p <= 8, stream a cudaStream_t.  Allocates nothing: its
- * scratch (partial sums, results, copies of the breakpoints and Gauss rule) is a
- * fixed 16384-double array in the library's device image, held by every GPU that
- * loads the library until the process exits; meshes with nx + ny + nz + 2(p+1) >
- * 14549 are rejected with TDKS_ERR_ARG.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress), so make the first call on each device
- * before any stream capture.  All calls share the array: calls that overlap on the
- * GPU race; serialize them.  Synchronizes the stream; returns TDKS_ERR_CUDA if a
- * CUDA call fails. */
+ * [nx*ny*nz][(p+1)^3] at the Gauss points (layout as above; the call reads exactly
+ * that many doubles and cannot check the length itself), X/Y/Z the host
+ * breakpoints, 1 <= p <= 8, stream a cudaStream_t of the current device (rho_q_dev
+ * must be memory of that device).  Allocates nothing: its scratch (partial sums,
+ * results, copies of the breakpoints and Gauss rule) is a fixed 16384-double array
+ * in the library's device image, held by every GPU that loads the library until the
+ * process exits; meshes with nx + ny + nz + 2(p+1) > 14549 are rejected with
+ * TDKS_ERR_ARG.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make the
+ * first call on each device before any stream capture, and do not call it on a
+ * device after cudaDeviceReset (the kept address would be stale).  All calls share
+ * the array: calls that overlap on the GPU race; serialize them.  Every call
+ * synchronizes the stream (it copies the three results to d_host); returns
+ * TDKS_ERR_CUDA if a CUDA call fails. */
 tdks_status tdks_dipole_noalloc(const double* rho_q_dev, int nx, int ny, int nz,
                                 const double* X, const double* Y, const double* Z, int p,
                                 void* stream, double d_host[3]);

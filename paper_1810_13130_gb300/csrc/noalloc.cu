@@ -2,8 +2,8 @@
 //
 // For callers that cannot allocate device memory: programs whose device memory
 // is owned by another allocator with a fixed budget, and code paths where an
-// allocation (which may also synchronize the device) is not allowed, such as a
-// real-time propagation loop after start-up.  It needs no context.
+// allocation is not allowed once running, such as a real-time propagation loop
+// after start-up.  It needs no context.  Every call synchronizes its stream.
 //
 // Its scratch -- the per-block partial sums, the 3 results, and copies of the
 // breakpoints and the Gauss rule -- lives in one file-scope __device__ array of
@@ -27,7 +27,9 @@ constexpr int kOffData = 3 * kNB + 8;
 static __device__ __align__(256) double g_noalloc_scratch[kMaxDoubles];
 
 std::mutex g_setup_mutex;
-double* g_scratch_ptr[128] = {nullptr};   // device address of the array, per device ordinal
+// Device address of the array, per device ordinal, looked up by the first call on
+// that device and kept for the life of the process (stale after cudaDeviceReset).
+double* g_scratch_ptr[128] = {nullptr};
 
 // Gauss-Legendre rule with 2 <= n <= 9 points in fixed-size storage (Newton on
 // the Legendre three-term recurrence, long double).

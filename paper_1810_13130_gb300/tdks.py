@@ -171,12 +171,23 @@ def _stream() -> int:
 
 def dipole_noalloc(rho: torch.Tensor, X, Y, Z, p: int) -> np.ndarray:
     """tdks_dipole_noalloc: the dipole without a context and without any device
-    allocation (fixed scratch inside the library); calls must not overlap."""
+    allocation (fixed scratch inside the library); calls must not overlap.
+
+    The C entry point reads nx*ny*nz*(p+1)^3 doubles from rho and has no length
+    argument, so the length is checked here before anything reaches the library.
+    The call runs on rho's device and on that device's current stream."""
     Xa, Ya, Za = _darr(X), _darr(Y), _darr(Z)
+    n_e = (len(Xa) - 1) * (len(Ya) - 1) * (len(Za) - 1)
+    if not isinstance(rho, torch.Tensor) or n_e < 1 or rho.numel() != n_e * (int(p) + 1) ** 3:
+        raise TDKSError(f"tdks_dipole_noalloc: rho must hold nx*ny*nz*(p+1)^3 = "
+                        f"{max(n_e, 0) * (int(p) + 1) ** 3} values")
+    ptr = _dev(rho, torch.float64, "rho")
     d = np.zeros(3)
-    st = lib().tdks_dipole_noalloc(_dev(rho, torch.float64, "rho"), len(Xa) - 1, len(Ya) - 1,
-                                   len(Za) - 1, _ptr(Xa), _ptr(Ya), _ptr(Za), int(p),
-                                   C.c_void_p(_stream()), _ptr(d))
+    with torch.cuda.device(rho.device):
+        st = lib().tdks_dipole_noalloc(ptr, len(Xa) - 1, len(Ya) - 1, len(Za) - 1, _ptr(Xa),
+                                       _ptr(Ya), _ptr(Za), int(p),
+                                       C.c_void_p(torch.cuda.current_stream(rho.device).cuda_stream),
+                                       _ptr(d))
     if st != 0:
         raise TDKSError(f"tdks_dipole_noalloc: {lib().tdks_status_string(st).decode()}")
     return d

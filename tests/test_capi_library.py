@@ -72,3 +72,24 @@ def test_binding_has_no_cpu_fallback(libpath):
         tdks.dipole_noalloc(rho, b, b, b, 2)
     with pytest.raises(tdks.TDKSError):
         tdks._dev(torch.zeros(4, dtype=torch.complex64), torch.complex128, "psi")
+
+
+def test_dipole_noalloc_rejects_a_short_density_before_the_library(monkeypatch):
+    """The allocation-free dipole reads nx*ny*nz*(p+1)^3 doubles with no length
+    argument: the binding must refuse a density of any other length before any call
+    into the library (none could then read past the tensor)."""
+    import numpy as np
+    import torch
+    from paper_1810_13130_gb300 import tdks
+
+    def no_library():
+        raise AssertionError("the library was reached")
+
+    monkeypatch.setattr(tdks, "lib", no_library)
+    X = np.linspace(-1.0, 1.0, 3)               # 2 x 2 x 2 elements, p = 2: 216 values
+    for n in (215, 217, 0):
+        with pytest.raises(tdks.TDKSError, match="nx\\*ny\\*nz"):
+            tdks.dipole_noalloc(torch.zeros(n, dtype=torch.float64), X, X, X, 2)
+    # the right length passes the length check and stops at the device check (CPU tensor)
+    with pytest.raises(tdks.TDKSError, match="CUDA tensor"):
+        tdks.dipole_noalloc(torch.zeros(216, dtype=torch.float64), X, X, X, 2)
