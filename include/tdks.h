@@ -377,6 +377,15 @@ const char* tdks_batch_last_error(const tdks_batch* b);
  * The batched engine does not take this option. */
 tdks_status tdks_set_lanczos(tdks_ctx* ctx, int reorth);
 
+/* Orbitals per CTA of the element kernel of every Hbar application of the context
+ * (the kernel of Eqs. 15, 21; a launch-shape setting, not part of the method).  The
+ * CTAs of the kernel form a grid of element blocks x orbital chunks; each CTA
+ * applies Hbar to its elements for orbs_per_cta orbitals in turn, reusing the
+ * potential, geometry and Loewdin scales of its elements.  0 (default): chosen per
+ * launch (the largest power of two that keeps at least 8 CTAs per SM); n > 0: n
+ * (at most the orbital count of the call).  Results do not depend on it. */
+tdks_status tdks_set_apply_tile(tdks_ctx* ctx, int orbs_per_cta);
+
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar
  * colour launches, element-orbital applications, and -- when timing is on --
  * the summed device time of the Hbar applications inside tdks_expm measured
@@ -391,6 +400,16 @@ typedef struct {
 } tdks_counters;
 tdks_status tdks_set_timing(tdks_ctx* ctx, int on);
 tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);
+
+/* Arithmetic peak of the current device for the roofline of the contraction
+ * kernels (no counterpart in the paper: a measurement utility).  prec TDKS_FP64 or
+ * TDKS_FP32: reps launches of ctas_per_sm (1..32) CTAs per SM x 256 threads, each
+ * thread running 8 independent chains of iters fused multiply-adds in that type,
+ * timed with CUDA events on stream (a cudaStream_t) after one untimed launch.
+ * tflops_host: 2 x FMAs / time in TFLOP/s; ms_host: time per launch (either may be
+ * NULL).  Allocates and frees a small output buffer; synchronizes. */
+tdks_status tdks_fma_probe(int prec, int ctas_per_sm, int iters, int reps, void* stream,
+                           double* tflops_host, double* ms_host);
 
 /* Allocation-free dipole (no counterpart in the paper; a service for callers that
  * cannot allocate device memory -- programs whose device memory belongs to another

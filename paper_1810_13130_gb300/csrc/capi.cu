@@ -520,6 +520,12 @@ tdks_status tdks_set_lanczos(tdks_ctx* c, int reorth) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_apply_tile(tdks_ctx* c, int orbs_per_cta) {
+  if (!c || orbs_per_cta < 0 || orbs_per_cta > 1024) return TDKS_ERR_ARG;
+  c->opc_force = orbs_per_cta;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_timing(tdks_ctx* c, int on) {
   if (!c) return TDKS_ERR_ARG;
   c->timing = on != 0;

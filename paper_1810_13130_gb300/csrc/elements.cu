@@ -1483,6 +1483,7 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   // (about four waves at two CTAs per SM, so the last partial wave costs little)
   int opc = 1;
   while (opc < a.n_orb && (long long)bpe * ((a.n_orb + 2 * opc - 1) / (2 * opc)) >= 8 * 152) opc *= 2;
+  if (c->opc_force > 0) opc = c->opc_force < a.n_orb ? c->opc_force : a.n_orb;
   const int ochunks = (a.n_orb + opc - 1) / opc;
   const T* tab = std::is_same<T, double>::value ? (const T*)c->d_tab
                  : std::is_same<T, float>::value ? (const T*)(kBF ? c->d_tabbf : c->d_tabf)

@@ -92,6 +92,7 @@ def lib():
         "tdks_propagate_host": [v, p, p, i, i, i, d, p, d, i, i, p],
         "tdks_set_timing": [v, i],
         "tdks_get_counters": [v, C.POINTER(Counters), i],
+        "tdks_fma_probe": [i, i, i, i, v, _dp, _dp],
         "tdks_last_error": [v],
         "tdks_status_string": [i],
         "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
@@ -99,6 +100,7 @@ def lib():
         "tdks_objective_backward": [v, i, _dp],
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
         "tdks_set_lanczos": [v, i],
+        "tdks_set_apply_tile": [v, i],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
         "tdks_apply_H_gll": [v, p, p, p, i],
         "tdks_nuclear_potential_nodes": [v, p],
@@ -136,8 +138,10 @@ def exported_symbols() -> list:
                         "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
+                        "tdks_fma_probe",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
+                        "tdks_set_apply_tile",
                         "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
                         "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
@@ -191,6 +195,16 @@ def dipole_noalloc(rho: torch.Tensor, X, Y, Z, p: int) -> np.ndarray:
     if st != 0:
         raise TDKSError(f"tdks_dipole_noalloc: {lib().tdks_status_string(st).decode()}")
     return d
+
+
+def fma_probe(prec: int, ctas_per_sm: int = 8, iters: int = 16384, reps: int = 10):
+    """tdks_fma_probe on the current device and stream: (TFLOP/s, ms per launch)."""
+    tf, ms = np.zeros(1), np.zeros(1)
+    st = lib().tdks_fma_probe(int(prec), int(ctas_per_sm), int(iters), int(reps),
+                              C.c_void_p(_stream()), _ptr(tf), _ptr(ms))
+    if st != 0:
+        raise TDKSError(f"tdks_fma_probe: {lib().tdks_status_string(st).decode()}")
+    return float(tf[0]), float(ms[0])
 
 
 class Context:
@@ -250,6 +264,10 @@ class Context:
 
     def set_lanczos(self, reorth: bool):
         self._check(lib().tdks_set_lanczos(self.h, int(bool(reorth))), "tdks_set_lanczos")
+
+    def set_apply_tile(self, orbs_per_cta: int):
+        """tdks_set_apply_tile: orbitals per CTA of the element kernel (0: automatic)."""
+        self._check(lib().tdks_set_apply_tile(self.h, int(orbs_per_cta)), "tdks_set_apply_tile")
 
     def get_counters(self, reset: bool = False) -> dict:
         c = Counters()

@@ -127,6 +127,23 @@ def config2() -> SystemConfig:
         dt=0.1, n_steps=500, tol=1e-10, k_max=64, seed=CONFIG2_SEED)
 
 
+MID_SEED = 18101306
+
+
+def config_mid() -> SystemConfig:
+    """Mid-size multi-orbital molecule: the structure of config2 (erf pseudopotential
+    atoms with Z_v = 4, 2-bohr hexahedra, p = 6, Hartree + LDA, kick along x, dt 0.1)
+    on [-8,8]^3 with 8^3 elements (103,823 DoF), 4 atoms in a 3-bohr ball and 8
+    orbitals (16 electrons, neutral).  The oracle can propagate it for tens of steps."""
+    b = uniform_breaks(-8.0, 8.0, 8)
+    R = seeded_atoms(4, 3.0, 1.5, MID_SEED)
+    return SystemConfig(
+        name="molecule_erf4_8x8x8_p6", X=b, Y=b.copy(), Z=b.copy(), p=6, n_orb=8,
+        occ=np.full(8, 2.0), atom_R=R, atom_Z=np.full(4, 4.0),
+        nuc_kind="erf", nuc_param=0.8, kick=1e-3, kick_dir=(1.0, 0.0, 0.0),
+        dt=0.1, n_steps=50, tol=1e-10, k_max=64, seed=MID_SEED)
+
+
 def config3() -> SystemConfig:
     """All-electron-like CH4 stand-in on a geometrically graded 24^3 mesh, p=8."""
     b = graded_breaks(20.0, 12, 1.25)
