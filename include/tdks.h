@@ -64,12 +64,19 @@ typedef enum {
   TDKS_FP32 = 1,   /* float contractions with float accumulation, FP64 I/O  */
   TDKS_DF64 = 2,   /* double-float (compensated float-pair) contractions:
                       ~48-bit accurate products and sums on the FP32 pipe   */
-  TDKS_BF16 = 3    /* accuracy study: every contraction operand (input, 1-D
+  TDKS_BF16 = 3,   /* accuracy study: every contraction operand (input, 1-D
                       operator coefficients, each contraction result feeding
                       the next) rounded to bfloat16, FP32 products and sums,
                       i.e. the arithmetic of a BF16 tensor-core contraction,
                       run on the CUDA cores (no speed claim).  Single-system
                       calls only: tdks_batch_create rejects it.             */
+  TDKS_MIXED = 4   /* relaxed precision inside each Lanczos exponential: the
+                      Hbar applications of iteration j use double-float
+                      contractions while some orbital's a-posteriori estimate
+                      of Eq. 38 from iteration j-1 exceeds relax * tol, FP32
+                      contractions after (see tdks_set_mixed); recombination
+                      and density as TDKS_DF64.  tdks_apply_H treats it as
+                      TDKS_DF64.  Single-system calls only.                 */
 } tdks_prec;
 
 typedef enum {
@@ -377,6 +384,17 @@ const char* tdks_batch_last_error(const tdks_batch* b);
  * The batched engine does not take this option. */
 tdks_status tdks_set_lanczos(tdks_ctx* ctx, int reorth);
 
+/* Switch level of TDKS_MIXED (no counterpart in the paper; a precision schedule for
+ * the Lanczos exponential of Eqs. 36-38).  With inexact matrix-vector products the
+ * error that the product of iteration j adds to exp(-i tau Hbar) psi is about
+ * |tau| ||psi|| |y_j| ||delta_j||, y = exp(-i tau T) e_1 and delta_j the product's
+ * error; the a-posteriori estimate eps_j = |tau| beta_j ||psi|| |y_j| measures that
+ * weight.  Products after the iteration whose estimate fell to relax * tol (for every
+ * active orbital) therefore use FP32 contractions (relative error ~1e-7 of
+ * ||Hbar||), the earlier ones double-float.  relax >= 0; default 1e5; 0 gives
+ * double-float throughout.  The stopping rule is unchanged. */
+tdks_status tdks_set_mixed(tdks_ctx* ctx, double relax);
+
 /* Orbitals per CTA of the element kernel of every Hbar application of the context
  * (the kernel of Eqs. 15, 21; a launch-shape setting, not part of the method).  The
  * CTAs of the kernel form a grid of element blocks x orbital chunks; each CTA
@@ -397,6 +415,7 @@ typedef struct {
   int64_t apply_elem_orb;
   double apply_ms;
   int64_t cg_iters;
+  int64_t apply_launches_fp32;   /* TDKS_MIXED: applications run with FP32 contractions */
 } tdks_counters;
 tdks_status tdks_set_timing(tdks_ctx* ctx, int on);
 tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);

@@ -149,10 +149,15 @@ tdks_status check_orb(tdks_ctx* c, int n_orb) {
 
 }  // namespace
 
+bool valid_prec(int prec) {
+  return prec == TDKS_FP64 || prec == TDKS_FP32 || prec == TDKS_DF64 || prec == TDKS_BF16 ||
+         prec == TDKS_MIXED;
+}
+
 // V_HXC = V_H[rho] + V_XC[rho] of the orbitals psi; rho left in c->d_rho.
 tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters, int prec) {
   const size_t nf = (size_t)(c->n_elem * c->nq3);
-  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec));
+  TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec == TDKS_MIXED ? TDKS_DF64 : prec));
   if (c->hartree) {
     TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters));
   } else {
@@ -409,12 +414,11 @@ tdks_status tdks_nuclear_potential(tdks_ctx* c, double* v) {
 tdks_status tdks_apply_H(tdks_ctx* c, const double* psi, double* out, int n_orb, int prec) {
   if (!c || !psi || !out) return TDKS_ERR_ARG;
   if (n_orb < 1) return tdks_fail(c, TDKS_ERR_ARG, "n_orb >= 1");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
-    return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (!valid_prec(prec)) return tdks_fail(c, TDKS_ERR_ARG, "precision");
   ApplyArgs a{(const double2*)psi, c->n_int, (double2*)out, c->n_int, n_orb, nullptr, 0, nullptr, 0,
               0, nullptr, 0, nullptr, 0, 0};
   c->n_apply_units += (int64_t)n_orb * c->n_elem;
-  return launch_hbar_apply(c, a, prec);
+  return launch_hbar_apply(c, a, prec == TDKS_MIXED ? TDKS_DF64 : prec);
 }
 
 tdks_status tdks_nuclear_potential_nodes(tdks_ctx* c, double* v_nodes) {
@@ -455,8 +459,7 @@ tdks_status tdks_expm(tdks_ctx* c, const double* in, double* out, int n_orb, dou
   if (!c || !in || !out) return TDKS_ERR_ARG;
   TDKS_TRY(check_orb(c, n_orb));
   if (!(tol > 0) || !std::isfinite(tau)) return tdks_fail(c, TDKS_ERR_ARG, "tol > 0, finite tau");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
-    return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (!valid_prec(prec)) return tdks_fail(c, TDKS_ERR_ARG, "precision");
   if (in != out)
     TDKS_CU(c, cudaMemcpyAsync(out, in, (size_t)n_orb * c->n_int * sizeof(double2),
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -520,6 +523,12 @@ tdks_status tdks_set_lanczos(tdks_ctx* c, int reorth) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_mixed(tdks_ctx* c, double relax) {
+  if (!c || !(relax >= 0) || !std::isfinite(relax)) return TDKS_ERR_ARG;
+  c->mixed_relax = relax;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_apply_tile(tdks_ctx* c, int orbs_per_cta) {
   if (!c || orbs_per_cta < 0 || orbs_per_cta > 1024) return TDKS_ERR_ARG;
   c->opc_force = orbs_per_cta;
@@ -540,9 +549,10 @@ tdks_status tdks_get_counters(tdks_ctx* c, tdks_counters* out, int reset) {
     out->apply_elem_orb = c->n_apply_units;
     out->apply_ms = c->apply_ms;
     out->cg_iters = c->n_cg;
+    out->apply_launches_fp32 = c->n_apply_fp32;
   }
   if (reset) {
-    c->n_launch = c->n_apply_launch = c->n_apply_units = c->n_cg = 0;
+    c->n_launch = c->n_apply_launch = c->n_apply_units = c->n_cg = c->n_apply_fp32 = 0;
     c->apply_ms = 0.0;
   }
   return TDKS_OK;
@@ -556,8 +566,7 @@ tdks_status magnus_step_impl(tdks_ctx* c, double2* psi, int n_orb, double dt, co
   TDKS_TRY(check_orb(c, n_orb));
   if (!c->propagation_ready) return tdks_fail(c, TDKS_ERR_ARG, "call tdks_init_propagation first");
   if (!(dt > 0) || !(tol > 0)) return tdks_fail(c, TDKS_ERR_ARG, "dt > 0 and tol > 0");
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_BF16)
-    return tdks_fail(c, TDKS_ERR_ARG, "precision");
+  if (!valid_prec(prec)) return tdks_fail(c, TDKS_ERR_ARG, "precision");
   const size_t vb = (size_t)n_orb * c->n_int * sizeof(double2);
   const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
   if (!c->d_psi_half) {

@@ -22,6 +22,7 @@
 // With a cap k_max the unconverged basis serves the largest sub-step
 // tau_rem / 2^m whose estimate meets the tolerance, and the recurrence restarts.
 #include <cmath>
+#include <cstddef>
 
 #include "elements.cuh"
 #include "tdks_internal.h"
@@ -75,6 +76,7 @@ __global__ void k_kry_init(KryOrb* kry, int n_orb, double tau) {
   K.nsub = 0;
   K.applies = 0;
   K.pad = 0;
+  K.err = INFINITY;
 }
 
 __global__ void k_norm_part(const double2* v, int64_t stride, long long n, const KryOrb* kry,
@@ -104,6 +106,7 @@ __global__ void k_kry_start(KryOrb* kry, const double* part, int64_t pstride, in
     const double nrm = sqrt(s);
     K.nrm = nrm;
     K.k = 0;
+    K.err = INFINITY;
     if (!isfinite(nrm)) {
       K.status = KRY_FAILED;
     } else if (nrm == 0.0) {
@@ -295,11 +298,13 @@ __device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, 
   __syncwarp();
   int decision = 0;   // 0 continue, 1 converged, 2 sub-step, -1 failed
   double tau_used = K.t_rem;
+  double est = INFINITY;
   if (!isfinite(beta)) {
     decision = -1;
   } else {
     const bool ok = cheb_exp_signed(m, K.t_rem, W);
     const double err = ok ? fabs(K.t_rem) * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
+    est = err;
     if (ok && (err <= tol || beta == 0.0)) {
       decision = 1;
     } else if (m >= kmax) {
@@ -324,6 +329,7 @@ __device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, 
     K.applies += 1;
     K.beta[j] = beta;
     K.k = m;
+    K.err = est;
     if (decision == 0) {
       K.s[j + 1] = 1.0 / beta;
     } else if (decision == 1) {
@@ -562,6 +568,7 @@ __global__ void k_bkry_init(const BSys* __restrict__ sys, const BOrb* __restrict
   K.nsub = 0;
   K.applies = 0;
   K.pad = 0;
+  K.err = INFINITY;
 }
 
 // partial ||v||^2 of the (re)starting orbitals, one block per chunk of n_int / n_rblk entries
@@ -791,7 +798,10 @@ static tdks_status ensure_reorth(tdks_ctx* c) {
 
 struct KrySummary {
   int k, status, k_total, nsub, applies, kseen;
+  double err;
 };
+static_assert(offsetof(KryOrb, err) - offsetof(KryOrb, k) == offsetof(KrySummary, err),
+              "KrySummary mirrors KryOrb from k to err");
 
 static tdks_status read_summary(tdks_ctx* c, const KryOrb* kry, int n_orb, KrySummary* h) {
   TDKS_CU(c, cudaMemcpy2DAsync(h, sizeof(KrySummary), &kry[0].k, sizeof(KryOrb),
@@ -851,8 +861,22 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
       double2* Vn = VW + (int64_t)j * n;
       // Hbar q_j and the three-term update fused: V_{j+1} = Hbar q_j - alpha_j q_j - beta q_{j-1}
       ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, kry, j, apart, ps, 1, Vm, sm, npart, ps, 0};
+      // TDKS_MIXED: the error a matrix-vector product of iteration j contributes to
+      // the exponential scales with the weight |y_j| of q_j, which the a-posteriori
+      // estimate of the previous iteration bounds (eps = tau beta ||psi|| |y|); once
+      // every active orbital's estimate is below relax * tol, the FP32 rounding of
+      // the remaining products is far below the tolerance (relaxed inexact Krylov
+      // products), so they run with FP32 contractions.  Double-float before that.
+      int pj = prec == TDKS_MIXED ? TDKS_DF64 : prec;
+      if (prec == TDKS_MIXED && j > 0) {
+        double emax = 0.0;
+        for (int o = 0; o < n_orb; ++o)
+          if (h[o].status == KRY_ACTIVE) emax = h[o].err > emax ? h[o].err : emax;
+        if (emax <= c->mixed_relax * tol) pj = TDKS_FP32;
+      }
+      if (pj == TDKS_FP32 && prec == TDKS_MIXED) c->n_apply_fp32 += 1;
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[0], c->stream));
-      TDKS_TRY(launch_hbar_apply(c, a, prec));
+      TDKS_TRY(launch_hbar_apply(c, a, pj));
       if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
       c->n_apply_units += (int64_t)n_active * c->n_elem;
       if (c->lanczos_reorth) {
@@ -883,7 +907,7 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
       for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
       if (!n_active) break;
     }
-    if (prec == TDKS_DF64)
+    if (prec == TDKS_DF64 || prec == TDKS_MIXED)
       k_kry_recomb_df<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb, kry);
     else
       k_kry_recomb<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb,

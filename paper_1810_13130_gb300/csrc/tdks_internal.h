@@ -24,6 +24,7 @@ struct KryOrb {
   int nsub;                    // sub-steps taken
   int applies;                 // Hbar applications on this orbital
   int pad;
+  double err;                  // last a-posteriori estimate of Eq. 38 (INFINITY before the first)
   double alpha[TDKS_KMAX];
   double beta[TDKS_KMAX];
   double s[TDKS_KMAX + 1];     // basis vector j is q_j = s[j] * V_j
@@ -113,10 +114,11 @@ struct tdks_ctx {
   void* kb = nullptr;           // nonlocal Kleinman-Bylander projectors (kb.cu)
   int lanczos_reorth = 0;       // 1: CGS2 re-orthogonalization of every new Lanczos vector
   int opc_force = 0;            // orbitals per CTA of the Hbar element kernel (0: chosen per launch)
+  double mixed_relax = 1e5;     // TDKS_MIXED: FP32 contractions once every estimate <= relax * tol
   double2* d_ro_part = nullptr; // its partial dots [n_orb][TDKS_KMAX][chunks]
   double2* d_ro_h = nullptr;    // its projections [n_orb][TDKS_KMAX]
   // counters
-  int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0;
+  int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0, n_apply_fp32 = 0;
   double apply_ms = 0.0;
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -254,6 +256,9 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
 tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int n_orb, double tau,
                         double tol, int kmax, int prec, int* k_used, int* kmax_seen,
                         int64_t* applies, int* nsub);
+
+// TDKS_FP64 .. TDKS_MIXED (capi.cu)
+bool valid_prec(int prec);
 
 // reduction helper used by several files
 tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);

@@ -18,8 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdks.so")
 
 # contraction arithmetic (tdks_prec): FP64; FP32; DF64 double-float (FP64-level,
-# on the FP32 pipe); BF16 = bfloat16 operands with FP32 sums (accuracy study only)
-FP64, FP32, DF64, BF16 = 0, 1, 2, 3
+# on the FP32 pipe); BF16 = bfloat16 operands with FP32 sums (accuracy study only);
+# MIXED = double-float Lanczos products until the a-posteriori estimate falls to
+# relax * tol, FP32 after (tdks_set_mixed)
+FP64, FP32, DF64, BF16, MIXED = 0, 1, 2, 3, 4
 PRECOND_FDM, PRECOND_JACOBI = 0, 1
 NUC_KIND = {"none": 0, "soft": 1, "erf": 2, "bare": 3, "harmonic": 4}
 _dp = C.POINTER(C.c_double)
@@ -48,7 +50,8 @@ class Stats(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_int64), ("apply_launches", C.c_int64),
-                ("apply_elem_orb", C.c_int64), ("apply_ms", C.c_double), ("cg_iters", C.c_int64)]
+                ("apply_elem_orb", C.c_int64), ("apply_ms", C.c_double), ("cg_iters", C.c_int64),
+                ("apply_launches_fp32", C.c_int64)]
 
 
 class TDKSError(RuntimeError):
@@ -101,6 +104,7 @@ def lib():
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
         "tdks_set_lanczos": [v, i],
         "tdks_set_apply_tile": [v, i],
+        "tdks_set_mixed": [v, d],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
         "tdks_apply_H_gll": [v, p, p, p, i],
         "tdks_nuclear_potential_nodes": [v, p],
@@ -141,7 +145,7 @@ def exported_symbols() -> list:
                         "tdks_fma_probe",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
-                        "tdks_set_apply_tile",
+                        "tdks_set_apply_tile", "tdks_set_mixed",
                         "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
                         "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
@@ -264,6 +268,10 @@ class Context:
 
     def set_lanczos(self, reorth: bool):
         self._check(lib().tdks_set_lanczos(self.h, int(bool(reorth))), "tdks_set_lanczos")
+
+    def set_mixed(self, relax: float):
+        """tdks_set_mixed: FP32 products once every Lanczos estimate <= relax * tol."""
+        self._check(lib().tdks_set_mixed(self.h, float(relax)), "tdks_set_mixed")
 
     def set_apply_tile(self, orbs_per_cta: int):
         """tdks_set_apply_tile: orbitals per CTA of the element kernel (0: automatic)."""

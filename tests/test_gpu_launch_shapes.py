@@ -145,3 +145,28 @@ def test_apply_tile_does_not_change_results():
     with pytest.raises(tdks.TDKSError):
         ctx.set_apply_tile(-1)
     ctx.close()
+
+
+@pytest.mark.parametrize("tile", [8, 3])
+def test_expm_relaxed_precision_matches_oracle(tile, expm_ref):
+    """TDKS_MIXED: double-float products until every active orbital's estimate of Eq. 38
+    is below relax * tol, FP32 products after.  The stopping rule is unchanged, so the
+    Krylov dimensions stay within one of the oracle's and the result within a few
+    tolerances; the FP32 share must be non-zero for the schedule to be exercised."""
+    from paper_1810_13130_gb300 import tdks
+    cfg, m, v, psi, ref, k_ref = expm_ref
+    ctx = tdks.Context.from_config(cfg)
+    ctx.set_apply_tile(tile)
+    ctx.set_potential(_cuda(v))
+    ctx.get_counters(reset=True)
+    out, k = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.MIXED)
+    cnt = ctx.get_counters()
+    assert 0 < cnt["apply_launches_fp32"] < cnt["apply_launches"]
+    assert all(abs(a - b) <= 1 for a, b in zip(k, k_ref))
+    err = np.abs(out.cpu().numpy() - ref).max(axis=1)
+    assert err.max() < 1e-9, err
+    ctx.set_mixed(0.0)                     # never relaxed: the double-float path
+    out_df, _ = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.MIXED)
+    ref_df, _ = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.DF64)
+    assert torch.equal(out_df, ref_df)
+    ctx.close()

@@ -11,7 +11,9 @@ The dipole error is the one the benchmark reports,
 (Sec. V, Eq. 30: the dipole relative to the dipole the kick induced).  Bounds:
 FP64 <= 1e-9 in the dipole and in the final orbitals (relative to their largest
 entry) with the oracle's Krylov dimensions in every step; the double-float
-contractions (the compensated mixed-precision form) <= 1e-6; FP32
+contractions (the compensated mixed-precision form) and the relaxed schedule
+(double-float Lanczos products until the a-posteriori estimate is small, FP32
+after) <= 1e-6; FP32
 contractions are measured and must stay finite and below 1e-3 (they are not
 expected to meet 1e-6).  The batched engine is held to the same bounds.
 """
@@ -90,10 +92,13 @@ def test_mixed_precision_dipole_error_vs_oracle(name, mk):
     s, _ = _gold(cfg)
     tile = 8 if name == "mid" else 0      # the benchmark's launch shape
     d_df, psi_df, _, _ = _propagate(cfg, tdks.DF64, tile)
+    d_mx, psi_mx, _, _ = _propagate(cfg, tdks.MIXED, tile)
     d_32, _, _, _ = _propagate(cfg, tdks.FP32, tile)
     e_df, e_32 = dipole_err(d_df, s["dipole"]), dipole_err(d_32, s["dipole"])
-    print(f"\n{cfg.name}: dipole error vs oracle DF64 {e_df:.3e}, FP32 {e_32:.3e} (bound 1e-6)")
-    assert e_df <= 1e-6
+    e_mx = dipole_err(d_mx, s["dipole"])
+    print(f"\n{cfg.name}: dipole error vs oracle DF64 {e_df:.3e}, MIXED {e_mx:.3e}, "
+          f"FP32 {e_32:.3e} (bound 1e-6)")
+    assert e_df <= 1e-6 and e_mx <= 1e-6
     assert np.isfinite(e_32) and e_32 < 1e-3
     ref = s["psibar_final"]
     assert np.abs(psi_df - ref).max() / np.abs(ref).max() < 1e-8
