@@ -39,6 +39,11 @@ struct Cfg {
   static constexpr int E = (256 / P2) < 1 ? 1 : (256 / P2);   // elements per CTA
 };
 
+// Byte offset of the cp.async prefetch buffer (16-byte entries) in dynamic shared
+// memory: the end of the element lines rounded up to 16 bytes.  With float lines
+// that end is only 8-byte aligned for odd P1 (E * 2 * P1^3 * 4 bytes).
+__host__ __device__ constexpr size_t pf_offset(size_t lines_end) { return (lines_end + 15) & ~size_t(15); }
+
 // ---------------------------------------------------------------------------
 // Hbar psibar, complex, contraction type T (double or float)
 //
@@ -440,9 +445,15 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
                                             a.part, a.part_stride, blockIdx.x);
 }
 
-// double-float: split element body (real lines, no register spills at two CTAs per SM)
+// split element body (real lines): double-float without register spills at two CTAs
+// per SM; FP32 in 64 registers, four CTAs (32 warps) per SM to hide the latency of its
+// light arithmetic
+template <typename T>
+struct SplitOcc {
+  static constexpr int value = std::is_same<T, float>::value ? 4 : 2;
+};
 template <int P1, typename T>
-__global__ void __launch_bounds__(256, 2) k_hbar_split(Geom g, const T* __restrict__ tab,
+__global__ void __launch_bounds__(256, SplitOcc<T>::value) k_hbar_split(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
                                               int orb_per_cta, Cx<T>* __restrict__ ev) {
   constexpr int P3 = Cfg<P1>::P3;
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(256, 2) k_hbar_split(Geom g, const T* __restri
   };
   hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
                               a.part_stride, blockIdx.x,
-                              reinterpret_cast<double2*>(smem + off + (size_t)blockDim.y * 2 * P3 * sizeof(T)));
+                              reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))));
 }
 
 // alpha_j = sum of the element partials (fixed order), for the active orbitals
@@ -886,7 +897,7 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restr
     };
     hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                                 static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk,
-                                reinterpret_cast<double2*>(smem + off + (size_t)blockDim.y * 2 * P3 * sizeof(T)));
+                                reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))));
   }
 }
 
@@ -1457,10 +1468,11 @@ template <int P1, typename T, bool kBF = false>
 tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  constexpr bool kSplit = std::is_same<T, Df>::value;
+  constexpr bool kSplit = std::is_same<T, Df>::value || (std::is_same<T, float>::value && !kBF);
   constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);   // shared-memory entry per point
-  const size_t smem = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line +
-                      (kSplit ? (size_t)E * P2 * P1 * sizeof(double2) : 0);   // + prefetch buffer
+  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  const size_t smem = kSplit ? pf_offset(lines_end) + (size_t)E * P2 * P1 * sizeof(double2)   // + prefetch buffer
+                             : lines_end;
   if constexpr (kSplit) {
     TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   } else {
@@ -1717,8 +1729,9 @@ static size_t hbar_batch_smem_t(int E) {
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   constexpr bool kSplit = std::is_same<T, Df>::value;
   constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);
-  return (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line +
-         (kSplit ? (size_t)E * Cfg<P1>::P2 * P1 * sizeof(double2) : 0);   // + prefetch buffer
+  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  return kSplit ? pf_offset(lines_end) + (size_t)E * Cfg<P1>::P2 * P1 * sizeof(double2)   // + prefetch buffer
+                : lines_end;
 }
 
 template <int P1>
