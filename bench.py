@@ -39,7 +39,7 @@ BF16_NOTE = ("bfloat16 operands with FP32 products and sums, emulated on the CUD
              "measure the accuracy of a BF16 tensor-core contraction: the rate is not that of a "
              "tensor-core kernel")
 MIXED_NOTE = ("relaxed precision inside each Lanczos exponential: double-float contractions "
-              "until every active orbital's a-posteriori estimate (Eq. 38) is <= 1e5 x tol, FP32 "
+              "until every active orbital's a-posteriori estimate (Eq. 38) is <= 1e8 x tol, FP32 "
               "contractions for the remaining products; double-float recombination and density")
 PROFILES = {"fp64": os.path.join(ROOT, "profiles", "hbar_fp64_molecule.txt"),
             "df64": os.path.join(ROOT, "profiles", "hbar_df64_molecule.txt")}

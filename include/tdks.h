@@ -391,7 +391,7 @@ tdks_status tdks_set_lanczos(tdks_ctx* ctx, int reorth);
  * error; the a-posteriori estimate eps_j = |tau| beta_j ||psi|| |y_j| measures that
  * weight.  Products after the iteration whose estimate fell to relax * tol (for every
  * active orbital) therefore use FP32 contractions (relative error ~1e-7 of
- * ||Hbar||), the earlier ones double-float.  relax >= 0; default 1e5; 0 gives
+ * ||Hbar||), the earlier ones double-float.  relax >= 0; default 1e8; 0 gives
  * double-float throughout.  The stopping rule is unchanged. */
 tdks_status tdks_set_mixed(tdks_ctx* ctx, double relax);
 

@@ -114,7 +114,7 @@ struct tdks_ctx {
   void* kb = nullptr;           // nonlocal Kleinman-Bylander projectors (kb.cu)
   int lanczos_reorth = 0;       // 1: CGS2 re-orthogonalization of every new Lanczos vector
   int opc_force = 0;            // orbitals per CTA of the Hbar element kernel (0: chosen per launch)
-  double mixed_relax = 1e5;     // TDKS_MIXED: FP32 contractions once every estimate <= relax * tol
+  double mixed_relax = 1e8;     // TDKS_MIXED: FP32 contractions once every estimate <= relax * tol
   double2* d_ro_part = nullptr; // its partial dots [n_orb][TDKS_KMAX][chunks]
   double2* d_ro_h = nullptr;    // its projections [n_orb][TDKS_KMAX]
   // counters

@@ -158,6 +158,8 @@ def test_expm_relaxed_precision_matches_oracle(tile, expm_ref):
     ctx = tdks.Context.from_config(cfg)
     ctx.set_apply_tile(tile)
     ctx.set_potential(_cuda(v))
+    # a switch level of 1e5 x tol: the FP32 products add far less than the tolerance
+    ctx.set_mixed(1e5)
     ctx.get_counters(reset=True)
     out, k = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.MIXED)
     cnt = ctx.get_counters()
@@ -165,6 +167,14 @@ def test_expm_relaxed_precision_matches_oracle(tile, expm_ref):
     assert all(abs(a - b) <= 1 for a, b in zip(k, k_ref))
     err = np.abs(out.cpu().numpy() - ref).max(axis=1)
     assert err.max() < 1e-9, err
+    # the default level (1e8 x tol): FP32 products once every estimate is <= 1e-2;
+    # each adds about 1e-6 of its estimate, so the exponential stays within 1e-7
+    ctx.set_mixed(1e8)
+    ctx.get_counters(reset=True)
+    out, k = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.MIXED)
+    cnt = ctx.get_counters()
+    assert cnt["apply_launches_fp32"] > 0
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-7
     ctx.set_mixed(0.0)                     # never relaxed: the double-float path
     out_df, _ = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.MIXED)
     ref_df, _ = ctx.expm(_cuda(psi), TAU, tol=1e-10, k_max=64, prec=tdks.DF64)
