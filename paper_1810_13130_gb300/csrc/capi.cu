@@ -34,6 +34,8 @@ Geom tdks_geom(const tdks_ctx* c) {
     g.sf[d] = c->d_sf[d];
   }
   g.gauss = c->d_tab + tab_off_eta(c->P1);
+  for (int d = 0; d < 3; ++d) g.ih[d] = c->d_ih[d];
+  g.wq = c->d_tab + tab_off_w(c->P1);
   return g;
 }
 
@@ -72,6 +74,7 @@ void free_ctx(tdks_ctx* c) {
     cudaFree(c->d_coord[d]);
     cudaFree(c->d_kd[d]);
     cudaFree(c->d_md[d]);
+    cudaFree(c->d_ih[d]);
   }
   cudaFree(c->d_tab);
   cudaFree(c->d_tabf);
@@ -297,6 +300,9 @@ tdks_status tdks_create(const tdks_mesh_desc* m, const tdks_system_desc* s, void
     if ((st = upload(c, &c->d_sf[d], svf)) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_kd[d], kd)) != TDKS_OK) return fail(st);
     if ((st = upload(c, &c->d_md[d], md)) != TDKS_OK) return fail(st);
+    std::vector<double> ih(nn[d]);
+    for (int e = 0; e < nn[d]; ++e) ih[e] = 1.0 / (br[d][e + 1] - br[d][e]);
+    if ((st = upload(c, &c->d_ih[d], ih)) != TDKS_OK) return fail(st);
   }
   c->n_int = (int64_t)c->Ni[0] * c->Ni[1] * c->Ni[2];
   c->n_elem = (int64_t)c->nx * c->ny * c->nz;

@@ -248,6 +248,9 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
   int ex = 0, ey = 0, ez = 0;
   const bool valid = plain_elem(g, eidx, ex, ey, ez);
   const long long n_elem = (long long)g.nx * g.ny * g.nz;
+  // Set-up of the element factors: the few FP64 products (no division, no FP64
+  // conversion: the FP64 unit of this part is 1/64 of the FP32 rate) rounded into T
+  // on the integer pipe.
   T fx = from_d<T>(0.0), fy = from_d<T>(0.0), fz = from_d<T>(0.0);
   T vx[P1];
 #pragma unroll
@@ -256,28 +259,28 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
     const double hx = g.brk[0][ex + 1] - g.brk[0][ex];
     const double hy = g.brk[1][ey + 1] - g.brk[1][ey];
     const double hz = g.brk[2][ez + 1] - g.brk[2][ez];
-    const double J = 0.125 * hx * hy * hz;
-    const double wl = to_d(sw[u]) * to_d(sw[v]);
-    fx = from_d<T>(hy * hz / (4.0 * hx) * wl);
-    fy = from_d<T>(hx * hz / (4.0 * hy) * wl);
-    fz = from_d<T>(hx * hy / (4.0 * hz) * wl);
+    const double wl4 = 0.25 * g.wq[u] * g.wq[v];
+    fx = d2t<T>(hy * hz * g.ih[0][ex] * wl4);
+    fy = d2t<T>(hx * hz * g.ih[1][ey] * wl4);
+    fz = d2t<T>(hx * hy * g.ih[2][ez] * wl4);
+    const double jw = 0.5 * hx * hy * hz * wl4;          // J wl, J = hx hy hz / 8
     const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * ez);
     const double* vp = vks + e * P3 + v * P2 + u * P1;      // x-line (qy = u, qz = v)
 #pragma unroll
-    for (int q = 0; q < P1; ++q) vx[q] = from_d<T>(vp[q] * J * wl * to_d(sw[q]));
+    for (int q = 0; q < P1; ++q) vx[q] = d2t<T>(vp[q] * (jw * g.wq[q]));
   }
   const long long plane = (long long)g.nix * g.niy;
   // gather: z-column (a = u, b = v); Loewdin scales of the column (once per CTA)
   constexpr bool kF32 = std::is_same<T, float>::value;
-  constexpr bool kDF = std::is_same<T, Df>::value;
   const int Ig = ex * g.p + u, Jg = ey * g.p + v;
   const bool inG = valid && Ig >= 1 && Ig <= g.nix && Jg >= 1 && Jg <= g.niy;
   const long long baseG = inG ? (long long)(Ig - 1) + (long long)g.nix * (Jg - 1) : 0;
+  const double sxy = inG ? g.s[0][Ig] * g.s[1][Jg] : 0.0;
   T gsc[P1];
 #pragma unroll
   for (int c = 0; c < P1; ++c) {
     const int K = ez * g.p + c;
-    gsc[c] = from_d<T>((inG && K >= 1 && K <= g.niz) ? g.s[0][Ig] * g.s[1][Jg] * g.s[2][K] : 0.0);
+    gsc[c] = d2t<T>((inG && K >= 1 && K <= g.niz) ? sxy * g.s[2][K] : 0.0);
   }
 
   // The z-columns of the next active orbital are copied into shared memory
@@ -309,9 +312,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
     double sc = 1.0;
     orb(o, in, sc);
     int on = o_end;   // next active orbital, found when its prefetch is issued
-    T scT;
-    if constexpr (kF32) scT = d2f_bits(sc);
-    else scT = from_d<T>(sc);
+    const T scT = d2t<T>(sc);
     T apt = from_d<T>(0.0);
     T* evr = reinterpret_cast<T*>(ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -397,11 +398,9 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
       __syncthreads();
     }
     if (part) {
-      double apart;
-      if constexpr (kF32) apart = f2d_bits(apt);
-      else apart = f2d_bits(apt.hi) + f2d_bits(apt.lo);
-      const double s = block_sum(apart, red);
-      if (threadIdx.x + blockDim.x * threadIdx.y == 0) part[(long long)o * part_stride + pslot] = s;
+      // the CTA's alpha partial summed in T (on the FP32 pipe), to FP64 once
+      const T s = block_sum_t(apt, reinterpret_cast<T*>(red));
+      if (threadIdx.x + blockDim.x * threadIdx.y == 0) part[(long long)o * part_stride + pslot] = t2d(s);
     }
     o = on;
   }
@@ -447,13 +446,13 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
 
 // split element body (real lines): double-float without register spills at two CTAs
 // per SM; FP32 in 64 registers, four CTAs (32 warps) per SM to hide the latency of its
-// light arithmetic
-template <typename T>
+// light arithmetic (three, 85 registers, for p >= 7, whose longer lines spill at 64)
+template <int P1, typename T>
 struct SplitOcc {
-  static constexpr int value = std::is_same<T, float>::value ? 4 : 2;
+  static constexpr int value = std::is_same<T, float>::value ? (P1 >= 8 ? 3 : 4) : 2;
 };
 template <int P1, typename T>
-__global__ void __launch_bounds__(256, SplitOcc<T>::value) k_hbar_split(Geom g, const T* __restrict__ tab,
+__global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
                                               int orb_per_cta, Cx<T>* __restrict__ ev) {
   constexpr int P3 = Cfg<P1>::P3;

@@ -342,4 +342,50 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// double -> contraction type on the integer pipe (float: round to nearest even; Df:
+// the 48-bit split of d2df_bits), and back (the Df pair summed in FP64).
+template <typename T>
+__device__ __forceinline__ T d2t(double x);
+template <>
+__device__ __forceinline__ float d2t<float>(double x) { return d2f_bits(x); }
+template <>
+__device__ __forceinline__ Df d2t<Df>(double x) { return d2df_bits(x); }
+__device__ __forceinline__ double t2d(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double t2d(Df x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
+
+__device__ __forceinline__ float shfl_down_t(unsigned mask, float v, int off) {
+  return __shfl_down_sync(mask, v, off);
+}
+__device__ __forceinline__ Df shfl_down_t(unsigned mask, Df v, int off) {
+  return Df{__shfl_down_sync(mask, v.hi, off), __shfl_down_sync(mask, v.lo, off)};
+}
+__device__ __forceinline__ float add_t(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ Df add_t(Df a, Df b) { return df_add(a, b); }
+
+// Block sum in float or double-float (the FP32 pipe), same fixed tree as block_sum;
+// result valid in thread 0.  `red` needs one T per warp.
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* red) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const int lane = tid & 31;
+  const int wbase = tid & ~31;
+  const int nin = (nthr - wbase) < 32 ? (nthr - wbase) : 32;
+  const unsigned mask = nin == 32 ? 0xffffffffu : ((1u << nin) - 1u);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T t = shfl_down_t(mask, v, off);
+    if (lane + off < nin) v = add_t(v, t);
+  }
+  if (lane == 0) red[tid >> 5] = v;
+  __syncthreads();
+  T s = red[0];
+  if (tid == 0) {
+    const int nw = (nthr + 31) >> 5;
+    for (int i = 1; i < nw; ++i) s = add_t(s, red[i]);
+  }
+  __syncthreads();
+  return s;
+}
+
 }  // namespace tdks

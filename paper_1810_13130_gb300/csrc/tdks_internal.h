@@ -54,6 +54,8 @@ struct Geom {
   const double* s[3];          // 1-D factors of M^-1/2 per full node index
   const float* sf[3];          // the same factors rounded to float
   const double* gauss;         // Gauss points on [-1, 1] (P1)
+  const double* ih[3];         // 1 / element width per element, per axis (n)
+  const double* wq;            // Gauss weights on [-1, 1] (P1)
 };
 
 struct tdks_ctx {
@@ -76,6 +78,7 @@ struct tdks_ctx {
   double* d_coord[3] = {nullptr, nullptr, nullptr};      // node coordinates
   double* d_kd[3] = {nullptr, nullptr, nullptr};         // sum K1_aa / h  (Jacobi diagonal)
   double* d_md[3] = {nullptr, nullptr, nullptr};         // sum h Mg_aa
+  double* d_ih[3] = {nullptr, nullptr, nullptr};         // 1 / element width per element
   double* d_tab = nullptr;     // double tables (layout in tables.cpp)
   float* d_tabf = nullptr;     // float copy
   float* d_tabdf = nullptr;    // double-float copy (hi, lo pairs)

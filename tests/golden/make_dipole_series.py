@@ -15,7 +15,11 @@ predictor-corrector Magnus step (Eqs. 25-26, Sec. VI.B) with adaptive Lanczos
 Per workload it stores the dipoles d(t_n), n = 0..N (Sec. V, Eq. 30), the
 Krylov dimension of both exponentials of every step and orbital, the Poisson
 CG iteration counts, the final orbitals, and the oracle's wall time on one
-thread of the machine that ran it.
+thread of the machine that ran it.  To keep the files small, a ground state
+written here is stored rounded to float32 (the propagation starts from exactly
+that rounded state), and for more than 2e5 orbital values the final orbitals
+are kept as a seeded sample of 8192 entries per orbital plus their projections
+<R_k, psi_a> onto three seeded random unit vectors R_k (synth.random_psi).
 
     OMP_NUM_THREADS=1 python tests/golden/make_dipole_series.py atom|mid
 """
@@ -46,9 +50,21 @@ def ground_state(cfg, mesh, n_iter):
     for a in range(psi.shape[0]):          # sign: largest component positive
         if psi[a, np.argmax(np.abs(psi[a]))] < 0:
             psi[a] = -psi[a]
+    psi = psi.astype(np.float32)
     np.savez_compressed(path, psibar=psi, eigenvalues=vals, scf_iterations=n_iter)
     print(path, vals, flush=True)
     return psi.astype(complex)
+
+
+def final_orbitals(cfg, psi):
+    """The final orbitals in full, or (large systems) a seeded sample and projections."""
+    if psi.size <= 200000:
+        return {"psibar_final": psi}
+    rng = np.random.default_rng(cfg.seed + 1)
+    idx = np.sort(rng.choice(psi.shape[1], 8192, replace=False))
+    R = synth.random_psi(3, psi.shape[1], seed=cfg.seed + 2)
+    return {"final_sample_idx": idx, "final_sample": psi[:, idx], "final_proj": psi @ R.conj().T,
+            "final_proj_seed": cfg.seed + 2}
 
 
 def series(cfg, n_scf):
@@ -71,7 +87,7 @@ def series(cfg, n_scf):
     out = os.path.join(HERE, f"series_{cfg.name}.npz")
     np.savez_compressed(out, dipole=np.array(dip), k_half=np.array(kh, dtype=np.int32),
                         k_full=np.array(kf, dtype=np.int32),
-                        cg_iters=np.array(prop.cg_iters, dtype=np.int32), psibar_final=psi,
+                        cg_iters=np.array(prop.cg_iters, dtype=np.int32), **final_orbitals(cfg, psi),
                         n_steps=cfg.n_steps, dt=cfg.dt, tol=cfg.tol, k_max=cfg.k_max,
                         kappa=cfg.kick, kick_dir=np.array(cfg.kick_dir), cg_tol=CG_TOL,
                         oracle_wall_s=wall, oracle_threads=1,

@@ -44,6 +44,21 @@ def _gold(cfg):
     return s, gs
 
 
+def final_err(psi, s):
+    """Final orbitals against the oracle's: all entries when stored in full, else the
+    seeded sample of entries (relative to its largest) and the projections onto the
+    seeded random unit vectors (|<R, dpsi>| <= ||dpsi||, relative to the largest)."""
+    if "psibar_final" in s:
+        ref = s["psibar_final"]
+        return float(np.abs(psi - ref).max() / np.abs(ref).max())
+    samp = s["final_sample"]
+    e1 = np.abs(psi[:, s["final_sample_idx"]] - samp).max() / np.abs(samp).max()
+    R = synth.random_psi(3, psi.shape[1], seed=int(s["final_proj_seed"]))
+    proj = s["final_proj"]
+    e2 = np.abs(psi @ R.conj().T - proj).max() / np.abs(proj).max()
+    return float(max(e1, e2))
+
+
 def dipole_err(d, ref):
     ind = np.abs(ref - ref[0]).max()
     return float(np.abs(np.asarray(d) - ref).max() / ind)
@@ -81,8 +96,7 @@ def test_fp64_series_matches_oracle(name, mk, tile):
     d, psi, kh, kf = _propagate(cfg, tdks.FP64, tile)
     assert np.array_equal(kh, s["k_half"].max(axis=1)) and np.array_equal(kf, s["k_full"].max(axis=1))
     assert dipole_err(d, s["dipole"]) < 1e-9
-    ref = s["psibar_final"]
-    assert np.abs(psi - ref).max() / np.abs(ref).max() < 1e-9
+    assert final_err(psi, s) < 1e-9
 
 
 @pytest.mark.parametrize("name,mk", [("atom", synth.config1), ("mid", synth.config_mid)])
@@ -100,8 +114,7 @@ def test_mixed_precision_dipole_error_vs_oracle(name, mk):
           f"FP32 {e_32:.3e} (bound 1e-6)")
     assert e_df <= 1e-6 and e_mx <= 1e-6
     assert np.isfinite(e_32) and e_32 < 1e-3
-    ref = s["psibar_final"]
-    assert np.abs(psi_df - ref).max() / np.abs(ref).max() < 1e-8
+    assert final_err(psi_df, s) < 1e-8
 
 
 @pytest.mark.parametrize("prec_name,bound", [("fp64", 1e-9), ("df64", 1e-6)])
