@@ -384,6 +384,18 @@ const char* tdks_batch_last_error(const tdks_batch* b);
  * The batched engine does not take this option. */
 tdks_status tdks_set_lanczos(tdks_ctx* ctx, int reorth);
 
+/* Lanczos loop of every exponential of the context (tdks_expm, the Magnus steps, the
+ * objective and its adjoint; Eqs. 36-38 -- an execution choice, not part of the method).
+ * on = 1 (default): the iterations of a sub-step are one CUDA graph launch, each
+ * iteration after the first a conditional node whose condition a one-block kernel sets
+ * from the Lanczos state of the previous iteration (some orbital still active; under
+ * TDKS_MIXED also the contraction arithmetic), so the host reads that state once per
+ * sub-step.  The graph is captured on first use for a given starting vector and
+ * settings and kept with the context.  on = 0: the host launches every iteration and
+ * reads the state after each.  Both run the same kernels in the same order, so the
+ * results are identical. */
+tdks_status tdks_set_device_loop(tdks_ctx* ctx, int on);
+
 /* Switch level of TDKS_MIXED (no counterpart in the paper; a precision schedule for
  * the Lanczos exponential of Eqs. 36-38).  With inexact matrix-vector products the
  * error that the product of iteration j adds to exp(-i tau Hbar) psi is about
@@ -416,6 +428,7 @@ typedef struct {
   double apply_ms;
   int64_t cg_iters;
   int64_t apply_launches_fp32;   /* TDKS_MIXED: applications run with FP32 contractions */
+  int64_t state_reads;           /* synchronizing reads of the Lanczos state by the host */
 } tdks_counters;
 tdks_status tdks_set_timing(tdks_ctx* ctx, int on);
 tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);

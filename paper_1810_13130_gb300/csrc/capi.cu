@@ -62,6 +62,7 @@ tdks_status upload(tdks_ctx* c, T** p, const std::vector<T>& h) {
 
 void free_ctx(tdks_ctx* c) {
   kb_free(c);
+  if (c) kgraph_free(c);
   if (c) {
     cudaFree(c->d_ro_part);
     cudaFree(c->d_ro_h);
@@ -529,6 +530,12 @@ tdks_status tdks_set_lanczos(tdks_ctx* c, int reorth) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_device_loop(tdks_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return TDKS_ERR_ARG;
+  c->device_loop = on;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_mixed(tdks_ctx* c, double relax) {
   if (!c || !(relax >= 0) || !std::isfinite(relax)) return TDKS_ERR_ARG;
   c->mixed_relax = relax;
@@ -556,9 +563,11 @@ tdks_status tdks_get_counters(tdks_ctx* c, tdks_counters* out, int reset) {
     out->apply_ms = c->apply_ms;
     out->cg_iters = c->n_cg;
     out->apply_launches_fp32 = c->n_apply_fp32;
+    out->state_reads = c->n_state_reads;
   }
   if (reset) {
     c->n_launch = c->n_apply_launch = c->n_apply_units = c->n_cg = c->n_apply_fp32 = 0;
+    c->n_state_reads = 0;
     c->apply_ms = 0.0;
   }
   return TDKS_OK;

@@ -1641,6 +1641,20 @@ tdks_status cross_t(tdks_ctx* c, const double2* mu, const double2* phi, int n_or
   return TDKS_OK;
 }
 
+tdks_status ensure_evec(tdks_ctx* c, int n_orb) {
+  const size_t need = (size_t)n_orb * c->n_elem * c->P1 * c->P1 * c->P1 * sizeof(Cx<double>);
+  if (need <= c->evec_bytes) return TDKS_OK;
+  cudaFree(c->d_evec);
+  c->d_evec = nullptr;
+  c->evec_bytes = 0;
+  if (cudaMalloc(&c->d_evec, need) != cudaSuccess) {
+    cudaGetLastError();
+    return tdks_fail(c, TDKS_ERR_NOMEM, "element-result buffer");
+  }
+  c->evec_bytes = need;
+  return TDKS_OK;
+}
+
 int hbar_blocks_per_color(const tdks_ctx* c) {
   int b = 0;
   switch (c->P1) {

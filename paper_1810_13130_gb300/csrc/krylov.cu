@@ -807,6 +807,7 @@ static tdks_status read_summary(tdks_ctx* c, const KryOrb* kry, int n_orb, KrySu
   TDKS_CU(c, cudaMemcpy2DAsync(h, sizeof(KrySummary), &kry[0].k, sizeof(KryOrb),
                                sizeof(KrySummary), n_orb, cudaMemcpyDeviceToHost, c->stream));
   TDKS_CU(c, cudaStreamSynchronize(c->stream));
+  c->n_state_reads += 1;
   return TDKS_OK;
 }
 
@@ -820,6 +821,283 @@ tdks_status run_expm(tdks_ctx* c, const double2* in, double2* out, int n_orb, do
 // kept alive alongside the first by the adjoint).  The basis V_0 = in (when no
 // sub-step is needed), V_1.. in the workspace, and the per-orbital state stay
 // valid until the next call on the same workspace.
+__global__ void k_kry_ctl(const KryOrb* __restrict__ kry, int n_orb, double theta, int mixed,
+                          cudaGraphConditionalHandle h64, cudaGraphConditionalHandle h32,
+                          int* __restrict__ n32) {
+  __shared__ double red[kThreads / 32];
+  int any = 0;
+  double emax = 0.0;
+  for (int o = threadIdx.x; o < n_orb; o += blockDim.x) {
+    if (kry[o].status == KRY_ACTIVE) {
+      any = 1;
+      const double e = kry[o].err;
+      emax = (e > emax || e != e) ? e : emax;     // NaN propagates (no FP32 products then)
+    }
+  }
+  any = __syncthreads_or(any);
+  for (int off = 16; off > 0; off >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, emax, off);
+    emax = (t > emax || t != t) ? t : emax;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) emax = (red[k] > emax || red[k] != red[k]) ? red[k] : emax;
+    emax = (red[0] > emax || red[0] != red[0]) ? red[0] : emax;
+    if (!mixed) {
+      cudaGraphSetConditional(h64, any ? 1u : 0u);
+    } else {
+      const bool f32 = any && emax <= theta;
+      cudaGraphSetConditional(h32, f32 ? 1u : 0u);
+      cudaGraphSetConditional(h64, (any && !f32) ? 1u : 0u);
+      if (f32) *n32 += 1;
+    }
+  }
+}
+
+__global__ void k_stamp(unsigned long long* t) {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  *t = v;
+}
+
+// Kernels of Lanczos iteration j on workspace VW: the Hbar application of q_j with the
+// fused three-term update (contraction arithmetic pj), the optional CGS2 passes, and the
+// small exponential with the stopping decision.  Timing of the application: stamp
+// (device loop) receives %globaltimer before and after it, ev (host loop) two events.
+static tdks_status iteration_kernels(tdks_ctx* c, KryOrb* kry, const double2* cur, double2* VW,
+                                     int64_t wsorb, long long n, int n_orb, int j, int kmax, int pj,
+                                     double tol, int nb, int nasm, unsigned long long* stamp,
+                                     cudaEvent_t* ev) {
+  const int64_t ps = c->part_stride;
+  double* apart = c->d_part;
+  double* npart = c->d_part + (int64_t)c->n_orb * ps;
+  const double2* Vj = (j == 0) ? cur : VW + (int64_t)(j - 1) * n;
+  const int64_t sj = (j == 0) ? n : wsorb;
+  const double2* Vm = (j == 1) ? cur : (j >= 2 ? VW + (int64_t)(j - 2) * n : nullptr);
+  const int64_t sm = (j == 1) ? n : wsorb;
+  double2* Vn = VW + (int64_t)j * n;
+  // Hbar q_j and the three-term update fused: V_{j+1} = Hbar q_j - alpha_j q_j - beta q_{j-1}
+  ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, kry, j, apart, ps, 1, Vm, sm, npart, ps, 0};
+  if (stamp) k_stamp<<<1, 1, 0, c->stream>>>(stamp + 2 * j);
+  if (ev) TDKS_CU(c, cudaEventRecord(ev[0], c->stream));
+  TDKS_TRY(launch_hbar_apply(c, a, pj));
+  if (stamp) k_stamp<<<1, 1, 0, c->stream>>>(stamp + 2 * j + 1);
+  if (ev) TDKS_CU(c, cudaEventRecord(ev[1], c->stream));
+  if (c->lanczos_reorth) {
+    TDKS_TRY(ensure_reorth(c));
+    for (int pass = 0; pass < 2; ++pass) {
+      k_ro_dot<<<dim3(kRoChunks, j + 1, n_orb), kThreads, 0, c->stream>>>(n, cur, n, VW, wsorb, j, kry,
+                                                                          c->d_ro_part);
+      k_ro_fin<<<dim3(j + 1, n_orb), 32, 0, c->stream>>>(kry, c->d_ro_part, kRoChunks, c->d_ro_h);
+      k_ro_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, cur, n, VW, wsorb, j, kry, c->d_ro_h);
+    }
+    // ||w||^2 after the passes (the assembly's and the nonlocal partials are stale)
+    k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(VW + (int64_t)j * n, wsorb, n, kry, npart, ps);
+    k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nb, nullptr, 0);
+  } else {
+    k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm, kb_norm_parts(c),
+                                           kb_norm_blocks(c));
+  }
+  TDKS_CU(c, cudaGetLastError());
+  return TDKS_OK;
+}
+
+// ---- the Lanczos loop of one sub-step on the device -------------------------------
+// The iterations j = 0 .. k_max-1 of a sub-step are captured once into a CUDA graph:
+// iteration 0 unconditionally, every later iteration as a conditional IF node (two
+// sibling nodes under TDKS_MIXED, one per contraction arithmetic).  After iteration j
+// a one-block kernel sets the conditions of iteration j+1: some orbital still active
+// and, under TDKS_MIXED, whether every active orbital's estimate is <= relax * tol.  An
+// iteration whose condition stays 0 is skipped by the graph, so one launch runs the
+// whole loop and the host reads the Lanczos state once per sub-step instead of once per
+// iteration.  Each iteration keeps its own launch parameters (the kernels are those of
+// the host-driven loop), so the results are identical.  Graphs are cached per
+// starting vector and settings.
+struct KGraph {
+  const double2* cur = nullptr;
+  const void* VW = nullptr;
+  const void* evec = nullptr;
+  const void* kb = nullptr;
+  int n_orb = 0, kmax = 0, prec = 0, reorth = 0, opc = 0, timing = 0;
+  int len = 0;                             // iterations captured (<= kmax)
+  double tol = 0.0, relax = 0.0;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct KGraphCache {
+  std::vector<KGraph> graphs;
+  cudaStream_t cap = nullptr, body = nullptr;
+  unsigned long long* d_stamp = nullptr;   // [2 * TDKS_KMAX]
+  int* d_n32 = nullptr;                    // FP32 iterations of the last launch
+  unsigned long long* h_stamp = nullptr;   // pinned copies
+  int* h_n32 = nullptr;
+  bool broken = false;                     // a capture failed: host-driven loop from now on
+  int len_hint = 16;                       // iterations to capture: the most needed so far + 8
+};
+
+static void kgraph_clear(KGraphCache* K) {
+  for (auto& G : K->graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+  }
+  K->graphs.clear();
+}
+
+void kgraph_free(tdks_ctx* c) {
+  KGraphCache* K = static_cast<KGraphCache*>(c->kgraph);
+  if (!K) return;
+  kgraph_clear(K);
+  if (K->cap) cudaStreamDestroy(K->cap);
+  if (K->body) cudaStreamDestroy(K->body);
+  cudaFree(K->d_stamp);
+  cudaFree(K->d_n32);
+  cudaFreeHost(K->h_stamp);
+  cudaFreeHost(K->h_n32);
+  delete K;
+  c->kgraph = nullptr;
+}
+
+static tdks_status kgraph_cache(tdks_ctx* c, KGraphCache** out) {
+  if (!c->kgraph) {
+    KGraphCache* K = new KGraphCache();
+    c->kgraph = K;
+    if (cudaStreamCreateWithFlags(&K->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&K->body, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&K->d_stamp, 2 * TDKS_KMAX * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&K->d_n32, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&K->h_stamp, 2 * TDKS_KMAX * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&K->h_n32, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      kgraph_free(c);
+      return tdks_fail(c, TDKS_ERR_NOMEM, "device Lanczos loop buffers");
+    }
+  }
+  *out = static_cast<KGraphCache*>(c->kgraph);
+  return TDKS_OK;
+}
+
+// Inside an active capture of stream `cap`: append IF nodes (one per handle) that all
+// depend on the current capture dependencies; returns their body graphs.  The capture
+// then continues after all of them.
+static tdks_status add_if_nodes(tdks_ctx* c, cudaStream_t cap, const cudaGraphConditionalHandle* h,
+                                int nh, cudaGraph_t* bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  TDKS_CU(c, cudaStreamGetCaptureInfo(cap, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return tdks_fail(c, TDKS_ERR_CUDA, "stream is not capturing");
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphNode_t nodes[2];
+  for (int i = 0; i < nh; ++i) {
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h[i];
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    TDKS_CU(c, cudaGraphAddNode(&nodes[i], g, dv.data(), nullptr, dv.size(), &p));
+    bodies[i] = p.conditional.phGraph_out[0];
+  }
+  TDKS_CU(c, cudaStreamUpdateCaptureDependencies(cap, nodes, nullptr, nh, cudaStreamSetCaptureDependencies));
+  return TDKS_OK;
+}
+
+// Capture of iterations 0 .. kmax-1 of a sub-step starting from `cur`.
+static tdks_status capture_loop(tdks_ctx* c, KGraphCache* K, KGraph& G, KryOrb* kry, double2* VW,
+                                int64_t wsorb, long long n, int nb, int nasm) {
+  const int kmax = G.kmax, n_orb = G.n_orb, L = G.len;
+  const bool mixed = G.prec == TDKS_MIXED;
+  const int p64 = mixed ? TDKS_DF64 : G.prec;
+  const double theta = G.relax * G.tol;
+  unsigned long long* stamp = G.timing ? K->d_stamp : nullptr;
+  std::vector<cudaGraphConditionalHandle> h64(kmax + 1), h32(kmax + 1);
+  TDKS_CU(c, cudaGraphCreate(&G.g, 0));
+  for (int j = 1; j < L; ++j) {
+    TDKS_CU(c, cudaGraphConditionalHandleCreate(&h64[j], G.g, 0, cudaGraphCondAssignDefault));
+    if (mixed) TDKS_CU(c, cudaGraphConditionalHandleCreate(&h32[j], G.g, 0, cudaGraphCondAssignDefault));
+  }
+  cudaStream_t saved = c->stream;
+  const int64_t save_launch = c->n_launch, save_apply = c->n_apply_launch;
+  TDKS_CU(c, cudaStreamBeginCaptureToGraph(K->cap, G.g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  c->stream = K->cap;
+  tdks_status st = TDKS_OK;
+  auto ctl = [&](int jn) {
+    k_kry_ctl<<<1, kThreads, 0, c->stream>>>(kry, n_orb, theta, mixed ? 1 : 0, h64[jn], h32[jn], K->d_n32);
+  };
+  st = iteration_kernels(c, kry, G.cur, VW, wsorb, n, n_orb, 0, kmax, p64, G.tol, nb, nasm, stamp, nullptr);
+  if (st == TDKS_OK && L > 1) ctl(1);
+  for (int j = 1; j < L && st == TDKS_OK; ++j) {
+    const int nv = mixed ? 2 : 1;
+    const cudaGraphConditionalHandle hh[2] = {h64[j], h32[j]};
+    cudaGraph_t bodies[2] = {nullptr, nullptr};
+    st = add_if_nodes(c, K->cap, hh, nv, bodies);
+    for (int v = 0; v < nv && st == TDKS_OK; ++v) {
+      if (cudaStreamBeginCaptureToGraph(K->body, bodies[v], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        st = tdks_fail(c, TDKS_ERR_CUDA, "loop body capture");
+        break;
+      }
+      c->stream = K->body;
+      st = iteration_kernels(c, kry, G.cur, VW, wsorb, n, n_orb, j, kmax, v == 1 ? TDKS_FP32 : p64, G.tol,
+                             nb, nasm, stamp, nullptr);
+      if (st == TDKS_OK && j + 1 < L) ctl(j + 1);
+      cudaGraph_t outb = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(K->body, &outb);
+      c->stream = K->cap;
+      if (st == TDKS_OK && e != cudaSuccess) st = tdks_fail(c, TDKS_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaGraph_t outg = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(K->cap, &outg);
+  c->stream = saved;
+  c->n_launch = save_launch;
+  c->n_apply_launch = save_apply;
+  if (st != TDKS_OK) return st;
+  if (e != cudaSuccess) return tdks_fail(c, TDKS_ERR_CUDA, std::string("loop capture: ") + cudaGetErrorString(e));
+  TDKS_CU(c, cudaGraphInstantiate(&G.exec, G.g, 0));
+  return TDKS_OK;
+}
+
+static tdks_status get_loop_graph(tdks_ctx* c, KGraphCache* K, const double2* cur, KryOrb* kry, double2* VW,
+                                  int64_t wsorb, long long n, int n_orb, int kmax, int len, int prec,
+                                  double tol, int nb, int nasm, KGraph** out) {
+  for (auto& G : K->graphs) {
+    if (G.cur == cur && G.VW == VW && G.evec == c->d_evec && G.kb == c->kb && G.n_orb == n_orb &&
+        G.kmax == kmax && G.len == len && G.prec == prec && G.reorth == c->lanczos_reorth && G.opc == c->opc_force &&
+        G.timing == (c->timing ? 1 : 0) && G.tol == tol && G.relax == c->mixed_relax) {
+      *out = &G;
+      return TDKS_OK;
+    }
+  }
+  if (K->graphs.size() >= 8) kgraph_clear(K);
+  TDKS_TRY(ensure_evec(c, n_orb));     // the capture must not reallocate the element results
+  K->graphs.emplace_back();
+  KGraph& G = K->graphs.back();
+  G.cur = cur;
+  G.VW = VW;
+  G.evec = c->d_evec;
+  G.kb = c->kb;
+  G.n_orb = n_orb;
+  G.kmax = kmax;
+  G.len = len;
+  G.prec = prec;
+  G.reorth = c->lanczos_reorth;
+  G.opc = c->opc_force;
+  G.timing = c->timing ? 1 : 0;
+  G.tol = tol;
+  G.relax = c->mixed_relax;
+  const tdks_status st = capture_loop(c, K, G, kry, VW, wsorb, n, nb, nasm);
+  if (st != TDKS_OK) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    K->graphs.pop_back();
+    return st;
+  }
+  *out = &K->graphs.back();
+  return TDKS_OK;
+}
+
 tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int n_orb, double tau,
                         double tol, int kmax, int prec, int* k_used, int* kmax_seen,
                         int64_t* applies, int* nsub) {
@@ -829,15 +1107,26 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
   const int bpc = hbar_blocks_per_color(c);
   TDKS_TRY(ensure_part(c, n_orb, 8 * (int64_t)bpc));
   TDKS_TRY(ensure_krylov(c, w, n_orb, kmax));
+  if (c->lanczos_reorth) TDKS_TRY(ensure_reorth(c));
   KryOrb* kry = c->d_kryw[w];
   double2* VW = c->d_Vw[w];
   const int64_t ps = c->part_stride;
-  double* apart = c->d_part;
   double* npart = c->d_part + (int64_t)c->n_orb * ps;
   const int nb = grid_for(n);
   const int nasm = assemble_blocks(c, n_orb);   // partials of ||w||^2 per orbital
   const int64_t wsorb = (int64_t)kmax * n;   // stride between orbitals in the workspace
   std::vector<KrySummary> h(n_orb);
+  // the device-driven loop, unless disabled or the stream is being captured by the caller
+  bool device_loop = c->device_loop != 0;
+  KGraphCache* K = nullptr;
+  if (device_loop) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) device_loop = false;
+  }
+  if (device_loop) {
+    TDKS_TRY(kgraph_cache(c, &K));
+    if (K->broken) device_loop = false;
+  }
   k_kry_init<<<(n_orb + 63) / 64, 64, 0, c->stream>>>(kry, n_orb, tau);
   c->n_launch += 1;
   TDKS_CU(c, cudaGetLastError());
@@ -852,60 +1141,81 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
     k_kry_start<<<n_orb, kThreads, 0, c->stream>>>(kry, npart, ps, nb);
     c->n_launch += 2;
     TDKS_CU(c, cudaGetLastError());
-    for (int j = 0; j < kmax; ++j) {
-      const double2* Vj0 = cur;   // V_0 of this sub-step (re-orthogonalization)
-      const double2* Vj = (j == 0) ? cur : VW + (int64_t)(j - 1) * n;
-      const int64_t sj = (j == 0) ? n : wsorb;
-      const double2* Vm = (j == 1) ? cur : (j >= 2 ? VW + (int64_t)(j - 2) * n : nullptr);
-      const int64_t sm = (j == 1) ? n : wsorb;
-      double2* Vn = VW + (int64_t)j * n;
-      // Hbar q_j and the three-term update fused: V_{j+1} = Hbar q_j - alpha_j q_j - beta q_{j-1}
-      ApplyArgs a{Vj, sj, Vn, wsorb, n_orb, kry, j, apart, ps, 1, Vm, sm, npart, ps, 0};
-      // TDKS_MIXED: the error a matrix-vector product of iteration j contributes to
-      // the exponential scales with the weight |y_j| of q_j, which the a-posteriori
-      // estimate of the previous iteration bounds (eps = tau beta ||psi|| |y|); once
-      // every active orbital's estimate is below relax * tol, the FP32 rounding of
-      // the remaining products is far below the tolerance (relaxed inexact Krylov
-      // products), so they run with FP32 contractions.  Double-float before that.
-      int pj = prec == TDKS_MIXED ? TDKS_DF64 : prec;
-      if (prec == TDKS_MIXED && j > 0) {
-        double emax = 0.0;
-        for (int o = 0; o < n_orb; ++o)
-          if (h[o].status == KRY_ACTIVE) emax = h[o].err > emax ? h[o].err : emax;
-        if (emax <= c->mixed_relax * tol) pj = TDKS_FP32;
+    int j0 = 0;                // first iteration left to the host
+    KGraph* G = nullptr;
+    const int len = device_loop ? (K->len_hint < kmax ? K->len_hint : kmax) : 0;
+    if (device_loop) {
+      if (get_loop_graph(c, K, cur, kry, VW, wsorb, n, n_orb, kmax, len, prec, tol, nb, nasm, &G) != TDKS_OK) {
+        // capture is not available here: the host-driven loop from now on
+        cudaGetLastError();
+        K->broken = true;
+        device_loop = false;
+        c->err.clear();
       }
-      if (pj == TDKS_FP32 && prec == TDKS_MIXED) c->n_apply_fp32 += 1;
-      if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[0], c->stream));
-      TDKS_TRY(launch_hbar_apply(c, a, pj));
-      if (c->timing) TDKS_CU(c, cudaEventRecord(c->ev[1], c->stream));
-      c->n_apply_units += (int64_t)n_active * c->n_elem;
-      if (c->lanczos_reorth) {
-        TDKS_TRY(ensure_reorth(c));
-        for (int pass = 0; pass < 2; ++pass) {
-          k_ro_dot<<<dim3(kRoChunks, j + 1, n_orb), kThreads, 0, c->stream>>>(n, Vj0, n, VW, wsorb, j, kry,
-                                                                              c->d_ro_part);
-          k_ro_fin<<<dim3(j + 1, n_orb), 32, 0, c->stream>>>(kry, c->d_ro_part, kRoChunks, c->d_ro_h);
-          k_ro_update<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, Vj0, n, VW, wsorb, j, kry, c->d_ro_h);
-        }
-        // ||w||^2 after the passes (the assembly's and the nonlocal partials are stale)
-        k_norm_part<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(VW + (int64_t)j * n, wsorb, n, kry, npart, ps);
-        k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nb, nullptr, 0);
-        c->n_launch += 8;
-      } else {
-        k_kry_exp<<<n_orb, 32, 0, c->stream>>>(j, kmax, tol, kry, npart, ps, nasm, kb_norm_parts(c),
-                                               kb_norm_blocks(c));
-      }
-      c->n_launch += 1;
-      TDKS_CU(c, cudaGetLastError());
+    }
+    if (G) {
+      std::vector<int> app0(n_orb);
+      for (int o = 0; o < n_orb; ++o) app0[o] = h[o].applies;
+      TDKS_CU(c, cudaMemsetAsync(K->d_n32, 0, sizeof(int), c->stream));
+      TDKS_CU(c, cudaGraphLaunch(G->exec, c->stream));
+      TDKS_CU(c, cudaMemcpyAsync(K->h_n32, K->d_n32, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      if (c->timing)
+        TDKS_CU(c, cudaMemcpyAsync(K->h_stamp, K->d_stamp, 2 * kmax * sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, c->stream));
       TDKS_TRY(read_summary(c, kry, n_orb, h.data()));
-      if (c->timing) {
-        float ms = 0.f;
-        TDKS_CU(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-        c->apply_ms += ms;
+      // work of the loop: applications per orbital, iterations run, FP32 iterations
+      int iters = 0;
+      for (int o = 0; o < n_orb; ++o) {
+        const int d = h[o].applies - app0[o];
+        c->n_apply_units += (int64_t)d * c->n_elem;
+        iters = d > iters ? d : iters;
       }
+      c->n_apply_launch += iters;
+      if (iters + 8 > K->len_hint) K->len_hint = ((iters + 8 + 7) / 8) * 8;
+      c->n_apply_fp32 += *K->h_n32;
+      c->n_launch += (int64_t)iters * (c->lanczos_reorth ? 11 : 4) + (iters > 0 ? iters - 1 : 0);
+      if (c->timing)
+        for (int j = 0; j < iters; ++j) c->apply_ms += 1e-6 * (double)(K->h_stamp[2 * j + 1] - K->h_stamp[2 * j]);
       n_active = 0;
       for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
-      if (!n_active) break;
+      j0 = n_active ? len : kmax;
+    }
+    {
+      // the host-driven loop: every iteration when the device loop is off, or the
+      // iterations beyond the captured length (the next capture is longer)
+      if (j0 > 0 && j0 < kmax) {
+        const int need = j0 + 16;
+        K->len_hint = ((need + 7) / 8) * 8;
+      }
+      for (int j = j0; j < kmax; ++j) {
+        // TDKS_MIXED: the error a matrix-vector product of iteration j contributes to
+        // the exponential scales with the weight |y_j| of q_j, which the a-posteriori
+        // estimate of the previous iteration bounds (eps = tau beta ||psi|| |y|); once
+        // every active orbital's estimate is below relax * tol, the FP32 rounding of
+        // the remaining products is far below the tolerance (relaxed inexact Krylov
+        // products), so they run with FP32 contractions.  Double-float before that.
+        int pj = prec == TDKS_MIXED ? TDKS_DF64 : prec;
+        if (prec == TDKS_MIXED && j > 0) {
+          double emax = 0.0;
+          for (int o = 0; o < n_orb; ++o)
+            if (h[o].status == KRY_ACTIVE) emax = (h[o].err > emax || h[o].err != h[o].err) ? h[o].err : emax;
+          if (emax <= c->mixed_relax * tol) pj = TDKS_FP32;
+        }
+        if (pj == TDKS_FP32 && prec == TDKS_MIXED) c->n_apply_fp32 += 1;
+        TDKS_TRY(iteration_kernels(c, kry, cur, VW, wsorb, n, n_orb, j, kmax, pj, tol, nb, nasm, nullptr,
+                                   c->timing ? c->ev : nullptr));
+        c->n_apply_units += (int64_t)n_active * c->n_elem;
+        c->n_launch += c->lanczos_reorth ? 8 : 1;
+        TDKS_TRY(read_summary(c, kry, n_orb, h.data()));
+        if (c->timing) {
+          float ms = 0.f;
+          TDKS_CU(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+          c->apply_ms += ms;
+        }
+        n_active = 0;
+        for (int o = 0; o < n_orb; ++o) n_active += (h[o].status == KRY_ACTIVE);
+        if (!n_active) break;
+      }
     }
     if (prec == TDKS_DF64 || prec == TDKS_MIXED)
       k_kry_recomb_df<<<dim3(nb, n_orb), kThreads, 0, c->stream>>>(n, out, n, cur, n, VW, wsorb, kry);

@@ -117,11 +117,14 @@ struct tdks_ctx {
   void* kb = nullptr;           // nonlocal Kleinman-Bylander projectors (kb.cu)
   int lanczos_reorth = 0;       // 1: CGS2 re-orthogonalization of every new Lanczos vector
   int opc_force = 0;            // orbitals per CTA of the Hbar element kernel (0: chosen per launch)
+  int device_loop = 1;          // Lanczos iterations of a sub-step as one CUDA graph (krylov.cu)
+  void* kgraph = nullptr;       // its cached graphs
   double mixed_relax = 1e8;     // TDKS_MIXED: FP32 contractions once every estimate <= relax * tol
   double2* d_ro_part = nullptr; // its partial dots [n_orb][TDKS_KMAX][chunks]
   double2* d_ro_h = nullptr;    // its projections [n_orb][TDKS_KMAX]
   // counters
   int64_t n_launch = 0, n_apply_launch = 0, n_apply_units = 0, n_cg = 0, n_apply_fp32 = 0;
+  int64_t n_state_reads = 0;
   double apply_ms = 0.0;
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -262,6 +265,11 @@ tdks_status run_expm_ws(tdks_ctx* c, int w, const double2* in, double2* out, int
 
 // TDKS_FP64 .. TDKS_MIXED (capi.cu)
 bool valid_prec(int prec);
+
+// krylov.cu: cached graphs of the device-driven Lanczos loop
+void kgraph_free(tdks_ctx* c);
+// elements.cu: the element-result buffer sized for n_orb orbitals of any contraction type
+tdks_status ensure_evec(tdks_ctx* c, int n_orb);
 
 // reduction helper used by several files
 tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);

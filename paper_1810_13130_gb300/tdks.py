@@ -51,7 +51,7 @@ class Stats(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_int64), ("apply_launches", C.c_int64),
                 ("apply_elem_orb", C.c_int64), ("apply_ms", C.c_double), ("cg_iters", C.c_int64),
-                ("apply_launches_fp32", C.c_int64)]
+                ("apply_launches_fp32", C.c_int64), ("state_reads", C.c_int64)]
 
 
 class TDKSError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
         "tdks_set_lanczos": [v, i],
         "tdks_set_apply_tile": [v, i],
         "tdks_set_mixed": [v, d],
+        "tdks_set_device_loop": [v, i],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
         "tdks_apply_H_gll": [v, p, p, p, i],
         "tdks_nuclear_potential_nodes": [v, p],
@@ -145,7 +146,7 @@ def exported_symbols() -> list:
                         "tdks_fma_probe",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
-                        "tdks_set_apply_tile", "tdks_set_mixed",
+                        "tdks_set_apply_tile", "tdks_set_mixed", "tdks_set_device_loop",
                         "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
                         "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
@@ -268,6 +269,10 @@ class Context:
 
     def set_lanczos(self, reorth: bool):
         self._check(lib().tdks_set_lanczos(self.h, int(bool(reorth))), "tdks_set_lanczos")
+
+    def set_device_loop(self, on: bool):
+        """tdks_set_device_loop: Lanczos iterations of a sub-step as one graph launch."""
+        self._check(lib().tdks_set_device_loop(self.h, int(bool(on))), "tdks_set_device_loop")
 
     def set_mixed(self, relax: float):
         """tdks_set_mixed: FP32 products once every Lanczos estimate <= relax * tol."""
