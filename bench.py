@@ -615,6 +615,8 @@ def ours(args, rank: int, world: int, local_rank: int):
                 "baseline": "per-system FP64 path on the same 64 systems"}
     if args.adjoint and args.prec == "fp64":
         line["adjoint"] = adjoint_section(tdks, torch)
+    if args.mixed and args.prec == "fp64":
+        line["contraction_stage"] = contraction_stage_section(tdks, torch)
     if bg is not None:
         res = bg.results()
         mol = res.get("molecule")
@@ -790,6 +792,30 @@ def adjoint_section(tdks, torch) -> dict:
             "backward_over_forward": (t2 - t1) / (t1 - t0),
             "grad_vs_central_fd_max_rel": float(np.abs(g - fd).max() / np.abs(fd).max()),
             "grad": g.tolist()}
+
+
+def contraction_stage_section(tdks, torch) -> dict:
+    """One 1-D contraction stage of the p = 6 element kernel (a 7 x 7 operator on 622,592
+    lines, 256 times in shared memory) in each arithmetic: CUDA-core FP32 and double-float,
+    tensor-core BF16 operands and three-TF32 products (mma); useful multiply-adds per
+    second and the error against an FP64 matrix power."""
+    import numpy as np
+    P1, n, reps = 7, 512 * 152 * 8, 256
+    rng = np.random.default_rng(7)
+    op, _ = np.linalg.qr(rng.standard_normal((P1, P1)))
+    x = rng.standard_normal((n, P1))
+    ref = x @ np.linalg.matrix_power(op, reps).T
+    xd = torch.from_numpy(x).cuda()
+    out = {"workload": "7x7 orthogonal operator, 622,592 lines, 256 applications in shared memory",
+           "useful_macs_per_launch": n * reps * P1 * P1}
+    names = {0: "fp32_cuda_cores", 1: "double_float_cuda_cores", 2: "bf16_tensor_cores",
+             3: "tf32x3_tensor_cores"}
+    for v, name in names.items():
+        y, ms = tdks.contraction_probe(v, op, xd, reps)
+        out[name] = {"ms": ms, "useful_tmac_per_s": n * reps * P1 * P1 / (ms * 1e-3) / 1e12,
+                     "rel_err_vs_fp64": float(np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max())}
+    out["mma_useful_fraction"] = {"bf16_m16n8k16": 49 / 128, "tf32x3_m16n8k8": 49 / (3 * 64)}
+    return out
 
 
 def batched_section(tdks, torch, args, local_rank: int) -> dict:

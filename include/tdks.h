@@ -433,6 +433,20 @@ typedef struct {
 tdks_status tdks_set_timing(tdks_ctx* ctx, int on);
 tdks_status tdks_get_counters(tdks_ctx* ctx, tdks_counters* out, int reset);
 
+/* One-dimensional contraction stage of the element kernels in four arithmetic forms (a
+ * measurement utility, no counterpart in the paper): y = M^reps x for n_lines lines of
+ * P1 values (x_dev, y_dev: [n_lines][P1] doubles, device; n_lines a multiple of 512),
+ * M the P1 x P1 operator op_host (row-major M[q][i], host; 2 <= P1 <= 8), every power
+ * applied in shared memory after one load, so the time is that of the stage's arithmetic
+ * and shared-memory traffic.  variant 0: FP32 FMAs on the CUDA cores; 1: double-float
+ * on the CUDA cores; 2: tensor cores with BF16 operands and FP32 accumulation
+ * (mma m16n8k16, lines as the M dimension, K and N padded to 16 and 8); 3: tensor cores,
+ * three TF32 products per product (mma m16n8k8, FP32-level products).  ms_host: device
+ * time of one launch after an untimed one (CUDA events).  Synchronizes. */
+tdks_status tdks_contraction_probe(int variant, int P1, const double* op_host, const double* x_dev,
+                                   double* y_dev, int64_t n_lines, int reps, void* stream,
+                                   double* ms_host);
+
 /* Arithmetic peak of the current device for the roofline of the contraction
  * kernels (no counterpart in the paper: a measurement utility).  prec TDKS_FP64 or
  * TDKS_FP32: reps launches of ctas_per_sm (1..32) CTAs per SM x 256 threads, each

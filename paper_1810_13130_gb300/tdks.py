@@ -96,6 +96,7 @@ def lib():
         "tdks_set_timing": [v, i],
         "tdks_get_counters": [v, C.POINTER(Counters), i],
         "tdks_fma_probe": [i, i, i, i, v, _dp, _dp],
+        "tdks_contraction_probe": [i, i, _dp, p, p, i64, i, v, _dp],
         "tdks_last_error": [v],
         "tdks_status_string": [i],
         "tdks_dipole_noalloc": [p, i, i, i, _dp, _dp, _dp, i, v, _dp],
@@ -143,7 +144,7 @@ def exported_symbols() -> list:
                         "tdks_apply_H", "tdks_density", "tdks_dipole", "tdks_hartree", "tdks_xc",
                         "tdks_expm", "tdks_kick", "tdks_init_propagation", "tdks_magnus_step",
                         "tdks_propagate_host", "tdks_set_timing", "tdks_get_counters",
-                        "tdks_fma_probe",
+                        "tdks_fma_probe", "tdks_contraction_probe",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
                         "tdks_set_apply_tile", "tdks_set_mixed", "tdks_set_device_loop",
@@ -210,6 +211,25 @@ def fma_probe(prec: int, ctas_per_sm: int = 8, iters: int = 16384, reps: int = 1
     if st != 0:
         raise TDKSError(f"tdks_fma_probe: {lib().tdks_status_string(st).decode()}")
     return float(tf[0]), float(ms[0])
+
+
+def contraction_probe(variant: int, op, x: torch.Tensor, reps: int, out: Optional[torch.Tensor] = None):
+    """tdks_contraction_probe on x's device and current stream: (M^reps x, ms per launch).
+    variant 0 FP32, 1 double-float, 2 BF16 tensor cores, 3 three-TF32 tensor cores."""
+    opa = _darr(op)
+    P1 = opa.shape[0]
+    if x.dim() != 2 or x.shape[1] != P1 or x.shape[0] % 512:
+        raise TDKSError("tdks_contraction_probe: x must be [n_lines][P1] with n_lines a multiple of 512")
+    out = torch.empty_like(x) if out is None else out
+    ms = np.zeros(1)
+    with torch.cuda.device(x.device):
+        st = lib().tdks_contraction_probe(int(variant), int(P1), _ptr(opa), _dev(x, torch.float64, "x"),
+                                          _dev(out, torch.float64, "out"), int(x.shape[0]), int(reps),
+                                          C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream),
+                                          _ptr(ms))
+    if st != 0:
+        raise TDKSError(f"tdks_contraction_probe: {lib().tdks_status_string(st).decode()}")
+    return out, float(ms[0])
 
 
 class Context:
