@@ -320,8 +320,11 @@ tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
  * (each system's axes must have <= 1024 interior nodes, else TDKS_ERR_ARG).
  *
  * tdks_batch_create: n_sys systems; meshes/systems as for tdks_create, dt[n_sys]
- *   (> 0), contraction precision prec (TDKS_FP64/FP32/DF64), Lanczos tolerance
- *   and k_max (2..128).  The batch owns one CUDA stream (tdks_batch_stream) on
+ *   (> 0), contraction precision prec (TDKS_FP64/FP32/DF64/MIXED), Lanczos tolerance
+ *   and k_max (2..128).  TDKS_MIXED chooses per orbital: an orbital's products are
+ *   double-float until its own a-posteriori estimate (Eq. 38) is <= 1e8 * tol, FP32
+ *   after (each persistent apply launch takes the orbitals of its type); recombination
+ *   and density double-float.  The batch owns one CUDA stream (tdks_batch_stream) on
  *   which all its work runs, the orbitals of every system and all workspaces
  *   (Krylov basis: n_orb x k_max x n_int complex per system).
  * tdks_batch_set_orbitals / get_orbitals: device copies of one system's block

@@ -41,6 +41,8 @@ struct Deg {
   int P1 = 0, E = 1, grid = 1, n_items = 0;
   BItem* d_items = nullptr;
   const void* tab = nullptr;
+  int grid32 = 1;                 // TDKS_MIXED: the FP32 launch over the same work list
+  const void* tab32 = nullptr;
 };
 
 }  // namespace
@@ -48,6 +50,7 @@ struct Deg {
 struct tdks_batch {
   int n_sys = 0, prec = 0, kmax = 64, cg_iters = 4, n_sm = 152;
   double tol = 1e-10;
+  double theta = -1.0;              // TDKS_MIXED: FP32 products once an estimate is <= theta
   cudaStream_t st = nullptr, st_body = nullptr;
   cudaStream_t fs[kFieldStreams] = {};   // capture-only fork streams (field work)
   cudaStream_t ds[kDegStreams] = {};     // capture-only fork streams (loop body)
@@ -116,6 +119,24 @@ tdks_status balloc(tdks_batch* b, T** p, size_t count) {
 tdks_status ctx_try(tdks_batch* b, tdks_ctx* c, tdks_status s) {
   if (s != TDKS_OK) b->err = c ? c->err : std::string("context");
   return s;
+}
+
+// contraction type of the apply launches (TDKS_MIXED: double-float, plus an FP32 launch)
+int apply_prec(const tdks_batch* b) { return b->prec == TDKS_MIXED ? TDKS_DF64 : b->prec; }
+// arithmetic of the density interpolation
+int field_prec(const tdks_batch* b) { return b->prec == TDKS_MIXED ? TDKS_DF64 : b->prec; }
+// ticket counters zeroed per pass: one per degree, two under TDKS_MIXED
+int n_tickets(const tdks_batch* b) { return b->prec == TDKS_MIXED ? 2 * kDegStreams : kDegStreams; }
+
+// the apply of degree class i on `sys` (both launches under TDKS_MIXED)
+cudaError_t apply_degree(const tdks_batch* b, int i, const BSys* sys, cudaStream_t st) {
+  const Deg& d = b->degs[i];
+  cudaError_t e = launch_hbar_batch(d.P1, apply_prec(b), sys, d.d_items, d.n_items, d.E, d.grid, d.tab,
+                                    b->d_qctr + i, st);
+  if (e == cudaSuccess && b->prec == TDKS_MIXED)
+    e = launch_hbar_batch(d.P1, TDKS_FP32, sys, d.d_items, d.n_items, d.E, d.grid32, d.tab32,
+                          b->d_qctr + kDegStreams + i, st);
+  return e;
 }
 
 void free_batch(tdks_batch* b) {
@@ -202,15 +223,18 @@ tdks_status build_degree(tdks_batch* b, Deg& d, int E) {
   B_TRY(b, balloc(b, &d.d_items, items.size()), "work list");
   B_CU(b, cudaMemcpy(d.d_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice));
   d.n_items = (int)items.size();
-  int occ = 0;
-  const cudaError_t ce = hbar_batch_occupancy(d.P1, b->prec, E, &occ);
-  if (ce != cudaSuccess || occ < 1) {
-    cudaGetLastError();
-    return bfail(b, TDKS_ERR_CUDA, "occupancy query of the batched apply (p = " + std::to_string(d.P1 - 1) +
-                                       ", E = " + std::to_string(E) + "): " + cudaGetErrorString(ce) +
-                                       ", blocks/SM " + std::to_string(occ));
+  for (int k = 0; k < (b->prec == TDKS_MIXED ? 2 : 1); ++k) {
+    const int pr = k == 0 ? apply_prec(b) : TDKS_FP32;
+    int occ = 0;
+    const cudaError_t ce = hbar_batch_occupancy(d.P1, pr, E, &occ);
+    if (ce != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      return bfail(b, TDKS_ERR_CUDA, "occupancy query of the batched apply (p = " + std::to_string(d.P1 - 1) +
+                                         ", E = " + std::to_string(E) + "): " + cudaGetErrorString(ce) +
+                                         ", blocks/SM " + std::to_string(occ));
+    }
+    (k == 0 ? d.grid : d.grid32) = std::max(1, std::min(d.n_items, occ * b->n_sm));
   }
-  d.grid = std::max(1, std::min(d.n_items, occ * b->n_sm));
   return TDKS_OK;
 }
 
@@ -225,17 +249,16 @@ tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphCon
   for (int i = 0; i < nd; ++i) {
     const Deg& d = b->degs[i];
     B_CU(b, cudaStreamWaitEvent(b->ds[i], b->body_fork_ev, 0));
-    B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, b->d_qctr + i,
-                              b->ds[i]));
+    B_CU(b, apply_degree(b, i, sys, b->ds[i]));
     B_CU(b, cudaEventRecord(b->body_join_ev[i], b->ds[i]));
   }
   for (int i = 0; i < nd; ++i) B_CU(b, cudaStreamWaitEvent(s, b->body_join_ev[i], 0));
   B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
   B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
-  B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, s));
+  B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, s));
   B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, s));
   B_CU(b, launch_bloop_control(h, sys, b->d_orbs, b->n_gorb, iter, kMaxSubPasses * b->kmax,
-                               b->d_ctrl + 2, b->d_qctr, kDegStreams, s));
+                               b->d_ctrl + 2, b->d_qctr, n_tickets(b), s));
   return TDKS_OK;
 }
 
@@ -297,7 +320,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   }
   B_CU(b, mark(1));
   B_CU(b, launch_bkry_init(b->d_half, b->d_orbs, b->n_gorb, 0.5, b->st));
-  B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->d_qctr, kDegStreams, b->st));
+  B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->d_qctr, n_tickets(b), b->st));
   B_TRY(b, add_loop(b, b->d_half, b->d_ctrl + 0, h1), "half step");
   B_CU(b, launch_bkry_stats(b->d_half, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
   B_CU(b, mark(2));
@@ -305,7 +328,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   B_TRY(b, fork_fields(b), "fork");
   for (int s = 0; s < b->n_sys; ++s) {
     tdks_ctx* c = b->ctx[s];
-    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err, b->prec)),
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi_half[s], b->n_orb[s], c->d_vtmp, b->cg_iters, err, field_prec(b))),
           "corrector");
     B_TRY(b, ctx_try(b, c, launch_combine(c, c->d_vks, c->d_vnuc, 1.0, c->d_vtmp, 0.0, nullptr, nullptr,
                                           zero)), "corrector");
@@ -313,7 +336,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   B_TRY(b, join_fields(b), "join");
   B_CU(b, mark(3));
   B_CU(b, launch_bkry_init(b->d_full, b->d_orbs, b->n_gorb, 1.0, b->st));
-  B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->d_qctr, kDegStreams, b->st));
+  B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->d_qctr, n_tickets(b), b->st));
   B_TRY(b, add_loop(b, b->d_full, b->d_ctrl + 1, h2), "full step");
   B_CU(b, launch_bkry_stats(b->d_full, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
   B_CU(b, mark(4));
@@ -323,7 +346,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
     tdks_ctx* c = b->ctx[s];
     const size_t fb = (size_t)(c->n_elem * c->nq3) * sizeof(double);
     B_CU(b, cudaMemcpyAsync(c->d_vhxc2, c->d_vhxc1, fb, cudaMemcpyDeviceToDevice, c->stream));
-    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err, b->prec)), "history");
+    B_TRY(b, ctx_try(b, c, vhxc_graph(c, b->psi[s], b->n_orb[s], c->d_vhxc1, b->cg_iters, err, field_prec(b))), "history");
     B_TRY(b, ctx_try(b, c, dipole_graph(c, c->d_rho, b->d_dip + 3 * (size_t)s, b->d_ctrl + 3,
                                         3 * (int64_t)b->n_sys)), "dipole");
   }
@@ -364,17 +387,17 @@ tdks_status time_apply(tdks_batch* b, const Deg& d, const std::vector<BItem>& it
   B_TRY(b, balloc(b, &di, items.size()), "tuning");
   cudaMemcpy(di, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice);
   int occ = 0;
-  hbar_batch_occupancy(d.P1, b->prec, E, &occ);
+  hbar_batch_occupancy(d.P1, apply_prec(b), E, &occ);
   const int grid = std::max(1, std::min((int)items.size(), std::max(occ, 1) * b->n_sm));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int* q = b->d_qctr;
   cudaMemsetAsync(q, 0, sizeof(int) * (reps + 1), b->st);
-  cudaError_t ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, q, b->st);
+  cudaError_t ce = launch_hbar_batch(d.P1, apply_prec(b), b->d_full, di, (int)items.size(), E, grid, d.tab, q, b->st);
   cudaEventRecord(e0, b->st);
   for (int r = 0; r < reps && ce == cudaSuccess; ++r)
-    ce = launch_hbar_batch(d.P1, b->prec, b->d_full, di, (int)items.size(), E, grid, d.tab, q + 1 + r, b->st);
+    ce = launch_hbar_batch(d.P1, apply_prec(b), b->d_full, di, (int)items.size(), E, grid, d.tab, q + 1 + r, b->st);
   cudaEventRecord(e1, b->st);
   cudaError_t se = cudaEventSynchronize(e1);
   float t = 0.f;
@@ -399,7 +422,7 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   if (!out) return TDKS_ERR_ARG;
   *out = nullptr;
   if (n_sys < 1 || !meshes || !systems || !dt) return TDKS_ERR_ARG;
-  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64) return TDKS_ERR_ARG;
+  if (prec != TDKS_FP64 && prec != TDKS_FP32 && prec != TDKS_DF64 && prec != TDKS_MIXED) return TDKS_ERR_ARG;
   if (k_max < 2 || k_max > TDKS_KMAX || !(tol > 0)) return TDKS_ERR_ARG;
   tdks_batch* b = new tdks_batch();
   b->n_sys = n_sys;
@@ -507,6 +530,8 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
     S.apart = b->apart[s];
     S.npart = b->npart[s];
     S.dt = dt[s];
+    S.mixed = prec == TDKS_MIXED ? 1 : 0;
+    if (prec == TDKS_MIXED) b->theta = c->mixed_relax * tol;   // the context default, 1e8 x tol
     b->h_half[s] = S;
     b->h_half[s].out = b->psi_half[s];
     b->h_full[s] = S;
@@ -519,8 +544,10 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
       deg_index[c->P1] = (int)b->degs.size();
       Deg d;
       d.P1 = c->P1;
-      d.tab = prec == TDKS_FP32 ? (const void*)c->d_tabf : prec == TDKS_DF64 ? (const void*)c->d_tabdf
-                                                                             : (const void*)c->d_tab;
+      d.tab = prec == TDKS_FP32 ? (const void*)c->d_tabf
+              : (prec == TDKS_DF64 || prec == TDKS_MIXED) ? (const void*)c->d_tabdf
+                                                          : (const void*)c->d_tab;
+      d.tab32 = c->d_tabf;
       b->degs.push_back(d);
     }
   }
@@ -763,16 +790,13 @@ tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]) {
     B_CU(b, cudaEventRecord(ev[0], b->st));
     B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
     B_CU(b, cudaEventRecord(ev[1], b->st));
-    for (size_t i = 0; i < b->degs.size(); ++i) {
-      const Deg& d = b->degs[i];
-      B_CU(b, launch_hbar_batch(d.P1, b->prec, sys, d.d_items, d.n_items, d.E, d.grid, d.tab, b->d_qctr + i, b->st));
-    }
+    for (size_t i = 0; i < b->degs.size(); ++i) B_CU(b, apply_degree(b, (int)i, sys, b->st));
     B_CU(b, cudaEventRecord(ev[2], b->st));
     B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, b->st));
     B_CU(b, cudaEventRecord(ev[3], b->st));
     B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, b->st));
     B_CU(b, cudaEventRecord(ev[4], b->st));
-    B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->st));
+    B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, b->st));
     B_CU(b, cudaEventRecord(ev[5], b->st));
     B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, b->st));
     B_CU(b, cudaEventRecord(ev[6], b->st));

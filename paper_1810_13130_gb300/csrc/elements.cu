@@ -241,7 +241,8 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
                                                int o_begin, int o_end, OrbFn orb,
                                                Cx<T>* __restrict__ ev, double* part,
                                                int64_t part_stride, long long pslot,
-                                                     double2* __restrict__ pfbuf) {
+                                                     double2* __restrict__ pfbuf,
+                                                     long long ev_ostride = 0) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   typedef Cx<T> V;
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
@@ -314,7 +315,9 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
     int on = o_end;   // next active orbital, found when its prefetch is issued
     const T scT = d2t<T>(sc);
     T apt = from_d<T>(0.0);
-    T* evr = reinterpret_cast<T*>(ev + ((long long)o * n_elem + eidx) * P3 + v * P2 + u * P1);
+    // element results of orbital o start ev_ostride entries apart (n_elem P1^3 by default)
+    T* evr = reinterpret_cast<T*>(ev + (long long)o * (ev_ostride > 0 ? ev_ostride : n_elem * P3) +
+                                  eidx * P3 + v * P2 + u * P1);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll 1
     for (int comp = 0; comp < 2; ++comp) {   // real part, then imaginary part
@@ -842,8 +845,14 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ 
   }
 }
 
+// Batched element results are kept at the orbital stride of 16-byte entries for every
+// contraction type, so that under TDKS_MIXED FP32 and double-float orbitals share the
+// buffer: entries of Cx<T> per orbital = n_elem P1^3 * omul<T>.
+template <typename T>
+__host__ __device__ constexpr int batch_omul() { return (int)(sizeof(double2) / sizeof(Cx<T>)); }
+
 template <int P1, typename T>
-__global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restrict__ sys,
+__global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_batch_split(const BSys* __restrict__ sys,
                                                     const BItem* __restrict__ items, int n_items,
                                                     const T* __restrict__ tab, int* __restrict__ qctr) {
   constexpr int P3 = Cfg<P1>::P3;
@@ -889,6 +898,8 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restr
     auto orb = [&](int o, const double2*& in, double& sc) -> bool {
       const KryOrb& K = S.kry[o];
       if (K.status != KRY_ACTIVE) return false;
+      // relaxed schedule: this launch takes the orbitals whose next product is of type T
+      if (S.mixed && K.f32 != (std::is_same<T, float>::value ? 1 : 0)) return false;
       const int j = K.k;
       in = bvec(S, K, o, j);
       sc = K.s[j];
@@ -896,7 +907,8 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch_split(const BSys* __restr
     };
     hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                                 static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk,
-                                reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))));
+                                reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))),
+                                S.n_elem * P3 * batch_omul<T>());
   }
 }
 
@@ -923,6 +935,7 @@ __global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
   const BSys& S = sys[w.sys];
   const KryOrb& K = S.kry[w.o];
   if (K.status != KRY_ACTIVE) return;
+  if (S.mixed && K.f32 != (std::is_same<T, float>::value ? 1 : 0)) return;
   const int j = K.k;
   const double ca = K.alpha[j] * K.s[j];
   const double cb = j > 0 ? K.beta[j - 1] * K.s[j - 1] : 0.0;
@@ -930,7 +943,8 @@ __global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
   const double2* qm = j > 0 ? bvec(S, K, w.o, j - 1) : nullptr;
   double2* out = S.Vw + ((long long)w.o * S.kmax + j) * S.n_int;
   const Geom g = S.g;
-  const Cx<T>* evo = static_cast<const Cx<T>*>(S.ev) + (long long)w.o * S.n_elem * S.P1 * S.P1 * S.P1;
+  const Cx<T>* evo = static_cast<const Cx<T>*>(S.ev) +
+                     (long long)w.o * S.n_elem * S.P1 * S.P1 * S.P1 * batch_omul<T>();
   double acc = 0.0;
   switch (S.P1) {   // uniform per block
 #define TDKS_BASM(P) \
@@ -1740,7 +1754,7 @@ template <int P1, typename T>
 static size_t hbar_batch_smem_t(int E) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
-  constexpr bool kSplit = std::is_same<T, Df>::value;
+  constexpr bool kSplit = !std::is_same<T, double>::value;
   constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);
   const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
   return kSplit ? pf_offset(lines_end) + (size_t)E * Cfg<P1>::P2 * P1 * sizeof(double2)   // + prefetch buffer
@@ -1774,7 +1788,7 @@ static cudaError_t hbar_batch_launch_t(const BSys* sys, const BItem* items, int 
   const size_t smem = hbar_batch_smem_t<P1, T>(E);
   // split body for double-float (see k_hbar_split), complex body otherwise
   void (*kern)(const BSys*, const BItem*, int, const T*, int*);
-  if constexpr (std::is_same<T, Df>::value) kern = k_hbar_batch_split<P1, T>;
+  if constexpr (!std::is_same<T, double>::value) kern = k_hbar_batch_split<P1, T>;
   else kern = k_hbar_batch<P1, T>;
   // the kernel also holds ~330 B of static shared memory: opt in for any large size
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1830,7 +1844,10 @@ cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_
   if (n_rows <= 0) return cudaSuccess;
   if (prec == TDKS_FP32) k_bassemble<float><<<n_rows, 128, 0, st>>>(sys, rows);
   else if (prec == TDKS_DF64) k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
-  else k_bassemble<double><<<n_rows, 128, 0, st>>>(sys, rows);
+  else if (prec == TDKS_MIXED) {   // each orbital's rows in the type of its last product
+    k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
+    k_bassemble<float><<<n_rows, 128, 0, st>>>(sys, rows);
+  } else k_bassemble<double><<<n_rows, 128, 0, st>>>(sys, rows);
   return cudaGetLastError();
 }
 

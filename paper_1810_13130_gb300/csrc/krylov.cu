@@ -288,7 +288,8 @@ __device__ bool cheb_exp_signed(int m, double tau, ChebWork& W) {
 // Decision after the apply of basis vector j (beta = ||w||): small exponential,
 // a-posteriori estimate, and continue / converged / sub-step / failed.  Called
 // by one full warp.
-__device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, ChebWork& W) {
+__device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, ChebWork& W,
+                           double theta = -1.0) {
   const int lane = threadIdx.x & 31;
   const int m = j + 1;
   for (int i = lane; i < m; i += 32) {
@@ -330,6 +331,7 @@ __device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, 
     K.beta[j] = beta;
     K.k = m;
     K.err = est;
+    K.f32 = (decision == 0 && est <= theta) ? 1 : 0;   // batched relaxed schedule
     if (decision == 0) {
       K.s[j + 1] = 1.0 / beta;
     } else if (decision == 1) {
@@ -569,6 +571,7 @@ __global__ void k_bkry_init(const BSys* __restrict__ sys, const BOrb* __restrict
   K.applies = 0;
   K.pad = 0;
   K.err = INFINITY;
+  K.f32 = 0;
 }
 
 // partial ||v||^2 of the (re)starting orbitals, one block per chunk of n_int / n_rblk entries
@@ -601,6 +604,7 @@ __global__ void k_bkry_start(const BSys* __restrict__ sys, const BOrb* __restric
     const double nrm = sqrt(t);
     K.nrm = nrm;
     K.k = 0;
+    K.f32 = 0;                    // the first product of a (sub-)step: double-float
     if (!isfinite(nrm)) {
       K.status = KRY_FAILED;
     } else if (nrm == 0.0) {
@@ -614,7 +618,8 @@ __global__ void k_bkry_start(const BSys* __restrict__ sys, const BOrb* __restric
 }
 
 // beta_j, small exponential and decision: one warp per orbital, j = K.k
-__global__ void k_bkry_exp(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, double tol) {
+__global__ void k_bkry_exp(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, double tol,
+                           double theta) {
   __shared__ ChebWork W;
   const BOrb b = orbs[blockIdx.x];
   const BSys& S = sys[b.sys];
@@ -626,7 +631,7 @@ __global__ void k_bkry_exp(const BSys* __restrict__ sys, const BOrb* __restrict_
   for (int k = lane; k < S.n_rblk; k += 32) v += np[k];
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   const int j = K.k;
-  kry_decide(K, j, S.kmax, tol, sqrt(v), W);
+  kry_decide(K, j, S.kmax, tol, sqrt(v), W, theta);
 }
 
 // out = ||psi|| sum_j y_j s_j V_j of converged / sub-stepped orbitals, one block per chunk
@@ -1266,14 +1271,15 @@ cudaError_t launch_bkry_prepare(const BSys* sys, const BOrb* orbs, int n, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n, double tol, cudaStream_t st) {
-  k_bkry_exp<<<n, 32, 0, st>>>(sys, orbs, tol);
+cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n, double tol, double theta,
+                            cudaStream_t st) {
+  k_bkry_exp<<<n, 32, 0, st>>>(sys, orbs, tol, theta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n, const BRow* rows, int n_rows,
                                int prec, cudaStream_t st) {
-  if (prec == TDKS_DF64) k_brecomb_df<<<n_rows, kThreads, 0, st>>>(sys, rows);
+  if (prec == TDKS_DF64 || prec == TDKS_MIXED) k_brecomb_df<<<n_rows, kThreads, 0, st>>>(sys, rows);
   else k_brecomb<<<n_rows, kThreads, 0, st>>>(sys, rows);
   k_bkry_after<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n);
   return cudaGetLastError();

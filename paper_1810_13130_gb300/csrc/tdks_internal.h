@@ -25,6 +25,8 @@ struct KryOrb {
   int applies;                 // Hbar applications on this orbital
   int pad;
   double err;                  // last a-posteriori estimate of Eq. 38 (INFINITY before the first)
+  int f32;                     // batched TDKS_MIXED: the next product of this orbital in FP32
+  int pad2;
   double alpha[TDKS_KMAX];
   double beta[TDKS_KMAX];
   double s[TDKS_KMAX + 1];     // basis vector j is q_j = s[j] * V_j
@@ -286,7 +288,7 @@ struct BSys {
   int P1, n_orb, kmax;
   int n_eblk;                  // element blocks of the apply (alpha partials per orbital)
   int n_rblk;                  // row blocks of assembly / norms / recombination
-  int pad0;
+  int mixed;                   // TDKS_MIXED batch: each orbital's product type follows KryOrb::f32
   long long n_int, n_elem;
   const double2* in;           // exponential input [n_orb][n_int]
   double2* out;                // output [n_orb][n_int] (may equal in)
@@ -317,7 +319,8 @@ cudaError_t launch_bkry_init(const BSys* sys, const BOrb* orbs, int n_orbs, doub
                              cudaStream_t st);
 cudaError_t launch_bkry_prepare(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
                                 int n_rows, cudaStream_t st);
-cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n_orbs, double tol,
+// theta >= 0 (TDKS_MIXED): an orbital whose estimate is <= theta takes FP32 products next
+cudaError_t launch_bkry_exp(const BSys* sys, const BOrb* orbs, int n_orbs, double tol, double theta,
                             cudaStream_t st);
 cudaError_t launch_bkry_finish(const BSys* sys, const BOrb* orbs, int n_orbs, const BRow* rows,
                                int n_rows, int prec, cudaStream_t st);
