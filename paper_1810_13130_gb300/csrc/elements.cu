@@ -840,6 +840,15 @@ __global__ void __launch_bounds__(256, 2) k_hbar_batch(const BSys* __restrict__ 
       sc = K.s[j];
       return true;
     };
+    {   // an item none of whose orbitals is active is skipped before the element set-up
+      bool any = false;
+      for (int o = w.o0; o < w.o1 && !any; ++o) {
+        const double2* in_o;
+        double sc_o;
+        any = orb(o, in_o, sc_o);
+      }
+      if (!any) continue;
+    }
     hbar_elem_body<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                           static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk);
   }
@@ -905,6 +914,16 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_batch_spli
       sc = K.s[j];
       return true;
     };
+    {   // an item none of whose orbitals takes a product of type T now is skipped before
+        // the element set-up
+      bool any = false;
+      for (int o = w.o0; o < w.o1 && !any; ++o) {
+        const double2* in_o;
+        double sc_o;
+        any = orb(o, in_o, sc_o);
+      }
+      if (!any) continue;
+    }
     hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                                 static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk,
                                 reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))),
