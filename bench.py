@@ -11,6 +11,7 @@ Krylov tolerance 1e-10.  Metric: orbital-steps/s (value) and H-psi GDoF/s.
   python bench.py --impl reference ...    # the CPU oracle on a bounded sample
   python bench.py --horizon 500           # the molecule's full 500 steps per precision
   python bench.py --apply-only --prec df64  # standalone Hbar applications
+  python bench.py --stage-only            # one contraction stage: CUDA cores vs tensor cores
 
 Inputs are synthetic and resident in HBM before the timed region; the working
 set (Krylov basis, 16 x 64 x 857k complex128 = 14 GB) is far larger than L2.
@@ -72,6 +73,8 @@ def parse():
     ap.add_argument("--horizon", type=int, default=0,
                     help="run the molecule workload for this many steps per contraction type "
                          "(its full horizon is 500) and report the dipole differences")
+    ap.add_argument("--stage-only", action="store_true",
+                    help="time the contraction-stage probe (CUDA cores vs tensor cores) only")
     ap.add_argument("--apply-only", action="store_true",
                     help="time standalone Hbar applications (16 orbitals) instead of steps")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -997,6 +1000,12 @@ def main():
         return
     if args.horizon > 0:
         horizon(args, local_rank)
+        return
+    if args.stage_only:
+        import torch
+        from paper_1810_13130_gb300 import tdks
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"mode": "stage_only", **contraction_stage_section(tdks, torch)}), flush=True)
         return
     ours(args, rank, world, local_rank)
 

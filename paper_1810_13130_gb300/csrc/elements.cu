@@ -443,6 +443,11 @@ __global__ void __launch_bounds__(256, 2) k_hbar(Geom g, const T* __restrict__ t
     in = a.in_base + (long long)o * a.in_stride;
     return true;
   };
+  if (a.kry) {   // a CTA whose orbitals have all left the recurrence skips the element set-up
+    bool any = false;
+    for (int o = o0; o < o1 && !any; ++o) any = a.kry[o].status == KRY_ACTIVE;
+    if (!any) return;
+  }
   hbar_elem_body<P1, T, decltype(orb), kBF>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev,
                                             a.part, a.part_stride, blockIdx.x);
 }
@@ -485,6 +490,11 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom
     in = a.in_base + (long long)o * a.in_stride;
     return true;
   };
+  if (a.kry) {   // a CTA whose orbitals have all left the recurrence skips the element set-up
+    bool any = false;
+    for (int o = o0; o < o1 && !any; ++o) any = a.kry[o].status == KRY_ACTIVE;
+    if (!any) return;
+  }
   hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
                               a.part_stride, blockIdx.x,
                               reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))));
