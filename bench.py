@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--horizon", type=int, default=0,
                     help="run the molecule workload for this many steps per contraction type "
                          "(its full horizon is 500) and report the dipole differences")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven Lanczos loop (for ncu launch lists: ncu cannot profile the "
+                         "kernel nodes of graphs with conditional nodes; the kernels are the same)")
     ap.add_argument("--stage-only", action="store_true",
                     help="time the contraction-stage probe (CUDA cores vs tensor cores) only")
     ap.add_argument("--apply-only", action="store_true",
@@ -358,10 +361,15 @@ def replica_throughput(units_local: float, t_local: float, dist=None, device: st
     return world * units_local / t, t
 
 
+HOST_LOOP = False   # --host-loop
+
+
 def _run_steps(tdks, torch, cfg, prec, steps, warmup, local_rank, psi0, dist=None, timing=True):
     """K timed Magnus steps of a fresh context from psi0 (kicked on the device)."""
     ctx = tdks.Context.from_config(cfg)
     ctx.set_cg(1e-10)
+    if HOST_LOOP:
+        ctx.set_device_loop(False)
     psi = torch.from_numpy(psi0).cuda()
     ctx.kick(psi, cfg.kick, cfg.kick_dir)
     ctx.d_init = ctx.init_propagation(psi)
@@ -985,7 +993,9 @@ def horizon(args, local_rank: int):
 
 
 def main():
+    global HOST_LOOP
     args = parse()
+    HOST_LOOP = args.host_loop
     if args.oracle_sample is not None:
         oracle_sample_main(args.oracle_sample)
         return
