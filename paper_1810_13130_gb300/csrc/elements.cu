@@ -226,6 +226,24 @@ __device__ __forceinline__ void hbar_elem_body(const Geom& g, const T* sB, const
   }
 }
 
+// Shared-memory layout of one element's lines in the split body: entry (a, b, c) at
+// c * PS + b * LS + a, the Gauss-space copy S2 at P1 * PS, the next element ES entries on.
+// The strides are padded (chosen by counting shared-memory wavefronts of the x-, y- and
+// z-line accesses of 32-thread warps that straddle elements, for 4- and 8-byte entries)
+// so that the line loads and stores of a warp fall into distinct banks as far as the
+// P1 x P1 thread planes allow: at p = 7 the wavefronts per request fall from 4.3 to 1.3,
+// at p = 6 from 1.8 to 1.6.
+template <int P1, typename T>
+struct SplitLayout {
+  static constexpr bool kF = sizeof(T) == 4;
+  static constexpr int LS = P1 == 8 || P1 == 9 ? 9 : P1;
+  static constexpr int PS = P1 == 5 ? 25 : P1 == 6 ? 39 : P1 == 7 ? (kF ? 56 : 52) : P1 == 8 ? 72
+                          : P1 == 9 ? (kF ? 81 : 89) : P1 * P1;
+  static constexpr int ES = P1 == 5 ? 253 : P1 == 6 ? (kF ? 484 : 468) : P1 == 7 ? (kF ? 785 : 737)
+                          : P1 == 8 ? 1152 : P1 == 9 ? (kF ? 1465 : 1617) : 2 * P1 * P1 * P1;
+  static_assert(PS >= P1 * LS && ES >= 2 * P1 * PS, "padded layout holds two element cubes");
+};
+
 // Split form of the element body for the double-float contractions: Hbar is real, so
 // the real and imaginary parts pass through the element one after the other.  Each
 // thread then holds real lines only, which halves the line registers and the shared
@@ -244,6 +262,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
                                                      double2* __restrict__ pfbuf,
                                                      long long ev_ostride = 0) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
+  constexpr int LS = SplitLayout<P1, T>::LS, PS = SplitLayout<P1, T>::PS;
   typedef Cx<T> V;
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
@@ -338,7 +357,7 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
       }
       // forward z, y, x
       cs_apply<P1>(sB, col, t);
-      store_line(t, S1 + v * P1 + u, P2);
+      store_line(t, S1 + v * LS + u, PS);
       __syncthreads();
       // the buffer was last read before this barrier: refill it for the next orbital
       if (comp == 1) {
@@ -348,14 +367,14 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
         while (on < o_end && !orb(on, in_n, sc_n)) ++on;
         if (on < o_end) issue(in_n);
       }
-      load_line(col, S1 + v * P2 + u, P1);
+      load_line(col, S1 + v * PS + u, LS);
       cs_apply<P1>(sB, col, t);
-      store_line(t, S2 + v * P2 + u, P1);
+      store_line(t, S2 + v * PS + u, LS);
       __syncthreads();
       T uq[P1];
-      load_line(col, S2 + v * P2 + u * P1, 1);
+      load_line(col, S2 + v * PS + u * LS, 1);
       cs_apply<P1>(sB, col, uq);
-      store_line(uq, S1 + v * P2 + u * P1, 1);          // U (Gauss-point values)
+      store_line(uq, S1 + v * PS + u * LS, 1);          // U (Gauss-point values)
       cs_apply<P1>(sK, uq, t);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
@@ -363,22 +382,22 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
         madd(r, fx, t[q]);
         t[q] = r;
       }
-      store_line(t, S2 + v * P2 + u * P1, 1);           // R
+      store_line(t, S2 + v * PS + u * LS, 1);           // R
       __syncthreads();
-      load_line(col, S1 + v * P2 + u, P1);
+      load_line(col, S1 + v * PS + u, LS);
       cs_apply<P1>(sK, col, t);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
-        T r = S2[v * P2 + q * P1 + u];
+        T r = S2[v * PS + q * LS + u];
         madd(r, fy, t[q]);
-        S2[v * P2 + q * P1 + u] = r;
+        S2[v * PS + q * LS + u] = r;
       }
       __syncthreads();
-      load_line(col, S1 + v * P1 + u, P2);
+      load_line(col, S1 + v * LS + u, PS);
       cs_apply<P1>(sK, col, t);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
-        T r = S2[q * P2 + v * P1 + u];
+        T r = S2[q * PS + v * LS + u];
         madd(r, fz, t[q]);
         uq[q] = r;
         dot_acc(apt, col[q], r);
@@ -386,13 +405,13 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
       __syncthreads();
       // backward z, y, x
       cs_apply<P1>(sBT, uq, t);
-      store_line(t, S1 + v * P1 + u, P2);
+      store_line(t, S1 + v * LS + u, PS);
       __syncthreads();
-      load_line(col, S1 + v * P2 + u, P1);
+      load_line(col, S1 + v * PS + u, LS);
       cs_apply<P1>(sBT, col, t);
-      store_line(t, S2 + v * P2 + u, P1);
+      store_line(t, S2 + v * PS + u, LS);
       __syncthreads();
-      load_line(col, S2 + v * P2 + u * P1, 1);
+      load_line(col, S2 + v * PS + u * LS, 1);
       cs_apply<P1>(sBT, col, t);
       if (valid) {
 #pragma unroll
@@ -472,8 +491,8 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom
   T* sK = sBT + CS;
   T* sw = sK + CS;
   const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
-  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
-  T* S2 = S1 + P3;
+  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * SplitLayout<P1, T>::ES;
+  T* S2 = S1 + P1 * SplitLayout<P1, T>::PS;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
@@ -497,7 +516,7 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom
   }
   hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
                               a.part_stride, blockIdx.x,
-                              reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))));
+                              reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * SplitLayout<P1, T>::ES * sizeof(T))));
 }
 
 // alpha_j = sum of the element partials (fixed order), for the active orbitals
@@ -883,8 +902,8 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_batch_spli
   T* sK = sBT + CS;
   T* sw = sK + CS;
   const size_t off = ((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15);
-  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * 2 * P3;
-  T* S2 = S1 + P3;
+  T* S1 = reinterpret_cast<T*>(smem + off) + (size_t)threadIdx.y * SplitLayout<P1, T>::ES;
+  T* S2 = S1 + P1 * SplitLayout<P1, T>::PS;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
@@ -936,7 +955,7 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_batch_spli
     }
     hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, S.vks, eidx, w.o0, w.o1, orb,
                                 static_cast<Cx<T>*>(S.ev), S.apart, S.n_eblk, w.eblk,
-                                reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * 2 * P3 * sizeof(T))),
+                                reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * SplitLayout<P1, T>::ES * sizeof(T))),
                                 S.n_elem * P3 * batch_omul<T>());
   }
 }
@@ -1511,8 +1530,8 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3, E = Cfg<P1>::E;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   constexpr bool kSplit = std::is_same<T, Df>::value || (std::is_same<T, float>::value && !kBF);
-  constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);   // shared-memory entry per point
-  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  constexpr size_t elem = kSplit ? (size_t)SplitLayout<P1, T>::ES * sizeof(T) : 2 * P3 * sizeof(Cx<T>);
+  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * elem;
   const size_t smem = kSplit ? pf_offset(lines_end) + (size_t)E * P2 * P1 * sizeof(double2)   // + prefetch buffer
                              : lines_end;
   if constexpr (kSplit) {
@@ -1784,8 +1803,8 @@ static size_t hbar_batch_smem_t(int E) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   constexpr bool kSplit = !std::is_same<T, double>::value;
-  constexpr size_t line = kSplit ? sizeof(T) : sizeof(Cx<T>);
-  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * 2 * P3 * line;
+  constexpr size_t elem = kSplit ? (size_t)SplitLayout<P1, T>::ES * sizeof(T) : 2 * P3 * sizeof(Cx<T>);
+  const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * elem;
   return kSplit ? pf_offset(lines_end) + (size_t)E * Cfg<P1>::P2 * P1 * sizeof(double2)   // + prefetch buffer
                 : lines_end;
 }
