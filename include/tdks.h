@@ -337,9 +337,23 @@ tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
  *   (1..32) launches of each candidate; writes up to cap choices (tile table)
  *   to out.
  *   Optional; without it the largest tile and one orbital per item are used.
+ * tdks_batch_tune_kmax: per-system Krylov caps.  The Lanczos loop of a system whose
+ *   a-posteriori estimate (Eq. 38) has not met the tolerance at its cap restarts
+ *   from the vector reached (sub-steps), which costs Hbar applications; a larger
+ *   basis for that system avoids them at the price of memory.  After at least one
+ *   tdks_batch_steps call, every system that took more than one sub-step in an
+ *   exponential (since creation, or since its cap was last raised) gets the cap
+ *   k_cap (above its current cap, <= 128), the systems with the most Hbar work
+ *   first, as long as the added Krylov basis
+ *   (n_orb x (k_cap - cap) x n_int complex128 per system) fits in mem_budget bytes
+ *   (< 0: half of the device's free memory); the others keep theirs.  A system
+ *   whose larger basis cannot be allocated keeps its cap.  Writes the caps
+ *   [n_sys] to kmax_out (may be NULL).  The orbitals are unchanged; later steps
+ *   take at most as many sub-steps as before and reach the same tolerance.
+ *   The step graph is rebuilt on the next tdks_batch_steps call.
  * tdks_batch_steps: n_steps steps of every system; dipoles [n_steps][n_sys][3].
  *   Synchronizes.  TDKS_ERR_NOT_CONVERGED if a Lanczos loop failed or hit its
- *   pass cap (16 k_max passes) or a Poisson solve did not converge.
+ *   pass cap (16 x the largest k_max passes) or a Poisson solve did not converge.
  * tdks_batch_stats: sum over orbital-vector Hbar applications of the system's
  *   interior DoF count, and the largest Krylov dimension seen. */
 typedef struct tdks_batch tdks_batch;
@@ -362,6 +376,7 @@ tdks_status tdks_batch_get_orbitals(tdks_batch* b, int sys, double* psi_dev);
 tdks_status tdks_batch_kick(tdks_batch* b, const double* kappa, const double* dir);
 tdks_status tdks_batch_init(tdks_batch* b, double* dip_host);
 tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out);
+tdks_status tdks_batch_tune_kmax(tdks_batch* b, int k_cap, int64_t mem_budget, int* kmax_out);
 tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host);
 tdks_status tdks_batch_stats(tdks_batch* b, int64_t* dof_applies, int* k_max_seen, int reset);
 /* Phase timing of the step graph (diagnostics): with timing on, the graph records

@@ -32,7 +32,7 @@
 
 namespace {
 
-constexpr int kMaxSubPasses = 16;   // loop cap = kMaxSubPasses * k_max passes
+constexpr int kMaxSubPasses = 16;   // loop cap = kMaxSubPasses * (largest k_max) passes
 constexpr int kFieldStreams = 16;   // parallel branches of the per-system field work
 constexpr int kDegStreams = 9;      // parallel branches of the per-degree applies
 std::string g_create_err;           // message of the last failed tdks_batch_create
@@ -48,7 +48,8 @@ struct Deg {
 }  // namespace
 
 struct tdks_batch {
-  int n_sys = 0, prec = 0, kmax = 64, cg_iters = 4, n_sm = 152;
+  int n_sys = 0, prec = 0, cg_iters = 4, n_sm = 152;
+  int kmax = 64;                    // largest per-system Krylov cap (BSys::kmax)
   double tol = 1e-10;
   double theta = -1.0;              // TDKS_MIXED: FP32 products once an estimate is <= theta
   cudaStream_t st = nullptr, st_body = nullptr;
@@ -74,6 +75,7 @@ struct tdks_batch {
   int* d_ctrl = nullptr;            // [0], [1]: pass counters, [2]: error bits, [3]: step, [4]: k seen
   int* d_qctr = nullptr;            // work ticket counters of the apply launches (one per degree)
   unsigned long long* d_dof = nullptr;
+  unsigned long long* d_sub = nullptr;   // per system: largest sub-step count, Hbar applies
   double* d_dip = nullptr;
   int dip_cap = 256;
   cudaGraph_t graph = nullptr;
@@ -151,7 +153,7 @@ void free_batch(tdks_batch* b) {
   for (auto* p : b->npart) cudaFree(p);
   for (auto& d : b->degs) cudaFree(d.d_items);
   void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_qctr,
-                  b->d_dof, b->d_dip};
+                  b->d_dof, b->d_sub, b->d_dip};
   for (void* p : ptrs) cudaFree(p);
   for (auto* c : b->ctx) tdks_destroy(c);
   for (auto& e : b->tev)
@@ -322,7 +324,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   B_CU(b, launch_bkry_init(b->d_half, b->d_orbs, b->n_gorb, 0.5, b->st));
   B_CU(b, launch_bloop_begin(h1, b->d_ctrl + 0, b->d_qctr, n_tickets(b), b->st));
   B_TRY(b, add_loop(b, b->d_half, b->d_ctrl + 0, h1), "half step");
-  B_CU(b, launch_bkry_stats(b->d_half, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  B_CU(b, launch_bkry_stats(b->d_half, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->d_sub, b->st));
   B_CU(b, mark(2));
   // corrector potential from the density of psi^{n-1/2}
   B_TRY(b, fork_fields(b), "fork");
@@ -338,7 +340,7 @@ tdks_status capture_step(tdks_batch* b, cudaGraphConditionalHandle h1, cudaGraph
   B_CU(b, launch_bkry_init(b->d_full, b->d_orbs, b->n_gorb, 1.0, b->st));
   B_CU(b, launch_bloop_begin(h2, b->d_ctrl + 1, b->d_qctr, n_tickets(b), b->st));
   B_TRY(b, add_loop(b, b->d_full, b->d_ctrl + 1, h2), "full step");
-  B_CU(b, launch_bkry_stats(b->d_full, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->st));
+  B_CU(b, launch_bkry_stats(b->d_full, b->d_orbs, b->n_gorb, b->d_dof, b->d_ctrl + 4, b->d_sub, b->st));
   B_CU(b, mark(4));
   // history and dipole of every system
   B_TRY(b, fork_fields(b), "fork");
@@ -561,6 +563,7 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   if (balloc(b, &b->d_half, n_sys) || balloc(b, &b->d_full, n_sys) || balloc(b, &b->d_orbs, orbs.size()) ||
       balloc(b, &b->d_rows, rows.size()) || balloc(b, &b->d_rows_asm, rows.size()) ||
       balloc(b, &b->d_ctrl, 8) || balloc(b, &b->d_qctr, 64) || balloc(b, &b->d_dof, 1) ||
+      balloc(b, &b->d_sub, 2 * (size_t)n_sys) ||
       balloc(b, &b->d_dip, (size_t)b->dip_cap * n_sys * 3))
     return fail(TDKS_ERR_NOMEM);
   // assembly items: larger systems first, so their many row blocks start early
@@ -574,6 +577,7 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   cudaMemset(b->d_ctrl, 0, 8 * sizeof(int));
   cudaMemset(b->d_qctr, 0, 64 * sizeof(int));
   cudaMemset(b->d_dof, 0, sizeof(unsigned long long));
+  cudaMemset(b->d_sub, 0, 2 * n_sys * sizeof(unsigned long long));
   for (Deg& d : b->degs)
     if (build_degree(b, d, emax_of(d.P1)) != TDKS_OK) return fail(TDKS_ERR_CUDA);
   if (upload_descriptors(b) != TDKS_OK) return fail(TDKS_ERR_CUDA);
@@ -713,6 +717,59 @@ tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int 
   } else if (n_out) {
     *n_out = (int)b->tiles.size();
   }
+  return TDKS_OK;
+}
+
+tdks_status tdks_batch_tune_kmax(tdks_batch* b, int k_cap, int64_t mem_budget, int* kmax_out) {
+  if (!b || k_cap < 2 || k_cap > TDKS_KMAX) return TDKS_ERR_ARG;
+  // per system, over its exponentials since creation or since its cap was last
+  // raised: the largest sub-step count and the Hbar applications
+  std::vector<unsigned long long> sub(2 * (size_t)b->n_sys);
+  B_CU(b, cudaStreamSynchronize(b->st));
+  B_CU(b, cudaMemcpy(sub.data(), b->d_sub, sub.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  bool stepped = false;
+  for (int s = 0; s < b->n_sys; ++s) stepped = stepped || sub[2 * s + 1] > 0;
+  if (!stepped) return bfail(b, TDKS_ERR_ARG, "run a step first (the caps follow its sub-steps)");
+  // systems whose exponentials restarted at their cap, by Hbar work
+  std::vector<std::pair<double, int>> cand;
+  for (int s = 0; s < b->n_sys; ++s) {
+    if (b->h_full[s].kmax >= k_cap || sub[2 * s] <= 1) continue;
+    const double P1 = b->ctx[s]->P1;
+    cand.emplace_back((double)sub[2 * s + 1] * (double)b->ctx[s]->n_elem * P1 * P1 * P1 * P1, s);
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first > y.first;
+  });
+  if (mem_budget < 0) {
+    size_t fr = 0, tot = 0;
+    B_CU(b, cudaMemGetInfo(&fr, &tot));
+    mem_budget = (int64_t)(fr / 2);
+  }
+  for (const auto& cs : cand) {
+    const int s = cs.second;
+    const size_t nv = (size_t)b->n_orb[s] * b->ctx[s]->n_int;
+    const int64_t add = (int64_t)(nv * (size_t)(k_cap - b->h_full[s].kmax) * sizeof(double2));
+    if (add > mem_budget) continue;
+    double2* nw = nullptr;
+    if (cudaMalloc((void**)&nw, nv * (size_t)k_cap * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    invalidate_graph(b);
+    cudaFree(b->Vw[s]);
+    b->Vw[s] = nw;
+    for (BSys* S : {&b->h_half[s], &b->h_full[s]}) {
+      S->Vw = nw;
+      S->kmax = k_cap;
+    }
+    B_CU(b, cudaMemset(b->d_sub + 2 * s, 0, 2 * sizeof(unsigned long long)));   // statistics of the new cap
+    mem_budget -= add;
+  }
+  b->kmax = 0;
+  for (int s = 0; s < b->n_sys; ++s) b->kmax = std::max(b->kmax, b->h_full[s].kmax);
+  B_TRY(b, upload_descriptors(b), "Krylov caps");
+  if (kmax_out)
+    for (int s = 0; s < b->n_sys; ++s) kmax_out[s] = b->h_full[s].kmax;
   return TDKS_OK;
 }
 

@@ -745,9 +745,10 @@ __global__ void k_bloop_control(cudaGraphConditionalHandle h, const BSys* __rest
   }
 }
 
-// orbital-vector applies x interior DoFs and the largest Krylov dimension of the pass
+// orbital-vector applies x interior DoFs and the largest Krylov dimension of the
+// exponential; per system its largest sub-step count and its applies
 __global__ void k_bkry_stats(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n,
-                             unsigned long long* dof_applies, int* kseen) {
+                             unsigned long long* dof_applies, int* kseen, unsigned long long* sys_sub) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const BOrb b = orbs[g];
@@ -755,6 +756,8 @@ __global__ void k_bkry_stats(const BSys* __restrict__ sys, const BOrb* __restric
   const KryOrb& K = S.kry[b.o];
   atomicAdd(dof_applies, (unsigned long long)K.applies * (unsigned long long)S.n_int);
   atomicMax(kseen, K.pad);
+  atomicMax(&sys_sub[2 * b.sys], (unsigned long long)K.nsub);
+  atomicAdd(&sys_sub[2 * b.sys + 1], (unsigned long long)K.applies);
 }
 
 int grid_for(long long n) {
@@ -1300,7 +1303,7 @@ cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, 
 }
 
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n, unsigned long long* dof_applies,
-                              int* kseen, cudaStream_t st) {
-  k_bkry_stats<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n, dof_applies, kseen);
+                              int* kseen, unsigned long long* sys_sub, cudaStream_t st) {
+  k_bkry_stats<<<(n + 63) / 64, 64, 0, st>>>(sys, orbs, n, dof_applies, kseen, sys_sub);
   return cudaGetLastError();
 }

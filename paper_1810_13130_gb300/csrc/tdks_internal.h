@@ -330,8 +330,11 @@ cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qct
 cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs,
                                  int n_orbs, int* iter, int cap, int* err, int* qctr, int n_q,
                                  cudaStream_t st);
+// sys_sub[2 s] = largest sub-step count of system s, sys_sub[2 s + 1] = its
+// orbital-vector Hbar applications (both accumulated until the host clears them)
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
-                              unsigned long long* dof_applies, int* kseen, cudaStream_t st);
+                              unsigned long long* dof_applies, int* kseen, unsigned long long* sys_sub,
+                              cudaStream_t st);
 // V_HXC of an orbital block (density, Hartree by the polling CG, LDA) into out (capi.cu)
 tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters,
                     int prec = TDKS_FP64);

@@ -121,6 +121,7 @@ def lib():
         "tdks_batch_kick": [v, _dp, _dp],
         "tdks_batch_init": [v, _dp],
         "tdks_batch_tune": [v, i, p, i, C.POINTER(i)],
+        "tdks_batch_tune_kmax": [v, i, i64, C.POINTER(i)],
         "tdks_batch_steps": [v, i, _dp],
         "tdks_batch_stats": [v, C.POINTER(i64), C.POINTER(i), i],
         "tdks_batch_last_error": [v],
@@ -153,7 +154,7 @@ def exported_symbols() -> list:
                         "tdks_batch_create", "tdks_batch_destroy",
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
-                        "tdks_batch_tune", "tdks_batch_steps", "tdks_batch_stats",
+                        "tdks_batch_tune", "tdks_batch_tune_kmax", "tdks_batch_steps", "tdks_batch_stats",
                         "tdks_batch_last_error", "tdks_batch_set_timing", "tdks_batch_phase_ms",
                         "tdks_batch_profile_pass",
                         "tdks_last_error", "tdks_status_string")]
@@ -638,6 +639,14 @@ class Batch:
                     "tdks_batch_tune")
         return [{"p": t.p, "n_orb": t.n_orb, "elems_per_cta": t.elems_per_cta,
                  "orbs_per_item": t.orbs_per_item, "ms": t.ms} for t in out[:n.value]]
+
+    def tune_kmax(self, k_cap: int = 128, mem_budget: int = -1) -> list:
+        """Per-system Krylov caps after a step: k_cap for the systems whose last
+        exponential took sub-steps, within mem_budget bytes of added basis (< 0:
+        half of the free device memory); returns the caps [n_sys]."""
+        out = (C.c_int * self.n_sys)()
+        self._check(lib().tdks_batch_tune_kmax(self.h, k_cap, mem_budget, out), "tdks_batch_tune_kmax")
+        return list(out)
 
     def steps(self, n_steps: int) -> np.ndarray:
         """n_steps steps of every system; dipoles [n_steps, n_sys, 3]."""

@@ -158,3 +158,51 @@ def test_batch_rejects_bad_arguments():
         b.steps(1)                                   # no init yet
     with pytest.raises(tdks.TDKSError):
         b.set_orbitals(0, torch.zeros(1, 3, dtype=torch.complex128, device="cuda"))
+
+
+def test_batch_krylov_caps_follow_the_substeps():
+    """tdks_batch_tune_kmax raises the Krylov cap of exactly the systems whose
+    exponential restarted at the cap (the per-system path at the same cap takes
+    sub-steps there), within the memory budget; the steps after it equal the
+    per-system path run with the same per-system caps."""
+    from paper_1810_13130_gb300 import tdks
+    cfgs = synth.small_batch()
+    psi0 = _initial(cfgs)
+    K0, K1 = 6, 16
+    b, d0 = _batch(cfgs, psi0, k_max=K0)
+    with pytest.raises(tdks.TDKSError):
+        b.tune_kmax(K1)                              # no step yet: nothing to go by
+    d1 = b.steps(1)
+    # which systems restart at K0: the per-system path's own sub-step count
+    ctxs, gs, subs = [], [], []
+    for k, c in enumerate(cfgs):
+        ctx = tdks.Context.from_config(c)
+        g = torch.from_numpy(psi0[k]).cuda()
+        ctx.kick(g, c.kick, c.kick_dir)
+        ctx.init_propagation(g)
+        st = ctx.magnus_step(g, c.dt, tol=1e-10, k_max=K0)
+        subs.append(st["substeps"] > 0)
+        ctxs.append(ctx)
+        gs.append(g)
+    assert any(subs) and not all(subs)
+    assert b.tune_kmax(K1, mem_budget=0) == [K0] * len(cfgs)
+    need = [c.n_orb * ((len(c.X) - 1) * c.p - 1) * ((len(c.Y) - 1) * c.p - 1) * ((len(c.Z) - 1) * c.p - 1)
+            * (K1 - K0) * 16 for c in cfgs]
+    total = sum(n for n, s in zip(need, subs) if s)
+    if sum(subs) > 1:
+        short = b.tune_kmax(K1, mem_budget=total - 1)  # one of them no longer fits
+        assert 0 < sum(k == K1 for k in short) < sum(subs)
+    caps = b.tune_kmax(K1, mem_budget=total)
+    assert caps == [K1 if s else K0 for s in subs]
+    dips = b.steps(2)
+    for k, c in enumerate(cfgs):
+        ref = [ctxs[k].magnus_step(gs[k], c.dt, tol=1e-10, k_max=caps[k]) for _ in range(2)]
+        assert _rel(b.get_orbitals(k).cpu().numpy(), gs[k].cpu().numpy()) < 1e-10
+        rd = np.array([r["dipole"] for r in ref])
+        ind = max(np.abs(rd - d0[k]).max(), 1e-300)
+        assert np.abs(dips[:, k] - rd).max() <= 1e-9 * ind + 1e-14
+        if caps[k] == K1:
+            assert all(r["substeps"] == 0 for r in ref) or max(r["k_full_max"] for r in ref) > K0
+        ctxs[k].close()
+    with pytest.raises(tdks.TDKSError):
+        b.tune_kmax(200)
