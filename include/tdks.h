@@ -231,8 +231,8 @@ tdks_status tdks_propagate_host(tdks_ctx* ctx, const double* psi_host_in,
  * Hbar application of the context (tdks_apply_H, tdks_expm, tdks_magnus_step, the
  * objective and its adjoint) includes Hbar_nl; n_atoms = 0 removes it.  Each atom's
  * projector columns are stored on the box of nodes where some entry exceeds 1e-16 of
- * the column maximum.  lmax in {0, 1}; a, b > 0.  Synchronizes.  The batched engine
- * does not take this term.
+ * the column maximum.  lmax in {0, 1}; a, b > 0.  Synchronizes.  tdks_batch_set_kb
+ * gives one system of a batch the same term.
  * tdks_kb_info: projector count, the denominators h_p (h_host, n_proj doubles, may be
  * NULL), the number of nodes covered by some box and the stored values. */
 tdks_status tdks_set_kb(tdks_ctx* ctx, int n_atoms, const double* R_host, double a, double b,
@@ -351,6 +351,12 @@ tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
  *   [n_sys] to kmax_out (may be NULL).  The orbitals are unchanged; later steps
  *   take at most as many sub-steps as before and reach the same tolerance.
  *   The step graph is rebuilt on the next tdks_batch_steps call.
+ * tdks_batch_set_kb: the nonlocal Kleinman-Bylander term of tdks_set_kb (same
+ *   arguments, same projectors and storage) for system sys of the batch; every later
+ *   step of that system applies Hbar + Hbar_nl in its Lanczos iterations (projection
+ *   with each orbital's own Krylov vector, alpha and the norm of the new vector
+ *   corrected as in the single-system path).  n_atoms = 0 removes it.  Synchronizes;
+ *   the step graph is rebuilt on the next tdks_batch_steps call.
  * tdks_batch_steps: n_steps steps of every system; dipoles [n_steps][n_sys][3].
  *   Synchronizes.  TDKS_ERR_NOT_CONVERGED if a Lanczos loop failed or hit its
  *   pass cap (16 x the largest k_max passes) or a Poisson solve did not converge.
@@ -377,6 +383,8 @@ tdks_status tdks_batch_kick(tdks_batch* b, const double* kappa, const double* di
 tdks_status tdks_batch_init(tdks_batch* b, double* dip_host);
 tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int cap, int* n_out);
 tdks_status tdks_batch_tune_kmax(tdks_batch* b, int k_cap, int64_t mem_budget, int* kmax_out);
+tdks_status tdks_batch_set_kb(tdks_batch* b, int sys, int n_atoms, const double* R_host, double a,
+                              double b_, const double c[2], int lmax);
 tdks_status tdks_batch_steps(tdks_batch* b, int n_steps, double* dip_host);
 tdks_status tdks_batch_stats(tdks_batch* b, int64_t* dof_applies, int* k_max_seen, int reset);
 /* Phase timing of the step graph (diagnostics): with timing on, the graph records

@@ -71,6 +71,12 @@ struct tdks_batch {
   int n_gorb = 0;
   BRow *d_rows = nullptr, *d_rows_asm = nullptr;
   int n_rows = 0;
+  // nonlocal term of the systems that have projectors: projection items, orbitals,
+  // node blocks of the gather
+  BKbItem* d_kb_items = nullptr;
+  BOrb* d_kb_orbs = nullptr;
+  BRow* d_kb_rows = nullptr;
+  int n_kb_items = 0, n_kb_orbs = 0, n_kb_rows = 0;
   std::vector<Deg> degs;
   int* d_ctrl = nullptr;            // [0], [1]: pass counters, [2]: error bits, [3]: step, [4]: k seen
   int* d_qctr = nullptr;            // work ticket counters of the apply launches (one per degree)
@@ -153,7 +159,7 @@ void free_batch(tdks_batch* b) {
   for (auto* p : b->npart) cudaFree(p);
   for (auto& d : b->degs) cudaFree(d.d_items);
   void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_qctr,
-                  b->d_dof, b->d_sub, b->d_dip};
+                  b->d_dof, b->d_sub, b->d_dip, b->d_kb_items, b->d_kb_orbs, b->d_kb_rows};
   for (void* p : ptrs) cudaFree(p);
   for (auto* c : b->ctx) tdks_destroy(c);
   for (auto& e : b->tev)
@@ -213,6 +219,36 @@ tdks_status upload_descriptors(tdks_batch* b) {
   return TDKS_OK;
 }
 
+// Work lists of the nonlocal term over the systems whose descriptors carry projectors.
+tdks_status build_kb_lists(tdks_batch* b) {
+  std::vector<BKbItem> items;
+  std::vector<BOrb> orbs;
+  std::vector<BRow> rows;
+  for (int s = 0; s < b->n_sys; ++s) {
+    if (!b->h_full[s].kb) continue;
+    int nblk = 0, nproj = 0;
+    kb_view(b->ctx[s], nullptr, &nblk, &nproj);
+    for (int o = 0; o < b->n_orb[s]; ++o) {
+      orbs.push_back(BOrb{s, o});
+      for (int p = 0; p < nproj; ++p) items.push_back(BKbItem{s, o, p, 0});
+      for (int r = 0; r < nblk; ++r) rows.push_back(BRow{s, o, r, 0});
+    }
+  }
+  auto put = [&](auto** dst, int* n, const auto& src) -> tdks_status {
+    cudaFree(*dst);
+    *dst = nullptr;
+    *n = (int)src.size();
+    if (src.empty()) return TDKS_OK;
+    B_TRY(b, balloc(b, dst, src.size()), "nonlocal work lists");
+    B_CU(b, cudaMemcpy(*dst, src.data(), src.size() * sizeof(src[0]), cudaMemcpyHostToDevice));
+    return TDKS_OK;
+  };
+  B_TRY(b, put(&b->d_kb_items, &b->n_kb_items, items), "nonlocal work lists");
+  B_TRY(b, put(&b->d_kb_orbs, &b->n_kb_orbs, orbs), "nonlocal work lists");
+  B_TRY(b, put(&b->d_kb_rows, &b->n_kb_rows, rows), "nonlocal work lists");
+  return TDKS_OK;
+}
+
 // (Re)build the work list of degree class d with elements-per-tile E and the
 // current per-system orbital blocks.
 tdks_status build_degree(tdks_batch* b, Deg& d, int E) {
@@ -244,6 +280,7 @@ tdks_status build_degree(tdks_batch* b, Deg& d, int E) {
 tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphConditionalHandle h) {
   cudaStream_t s = b->st_body;
   B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, s));
+  B_CU(b, launch_bkb_project(sys, b->d_kb_items, b->n_kb_items, s));
   // the degree classes touch disjoint systems: concurrent branches, so that the
   // tail of one persistent grid overlaps the next
   const int nd = (int)b->degs.size();
@@ -256,7 +293,9 @@ tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphCon
   }
   for (int i = 0; i < nd; ++i) B_CU(b, cudaStreamWaitEvent(s, b->body_join_ev[i], 0));
   B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
+  B_CU(b, launch_bkb_alpha(sys, b->d_kb_orbs, b->n_kb_orbs, s));
   B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
+  B_CU(b, launch_bkb_add(sys, b->d_kb_rows, b->n_kb_rows, s));
   B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, s));
   B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, s));
   B_CU(b, launch_bloop_control(h, sys, b->d_orbs, b->n_gorb, iter, kMaxSubPasses * b->kmax,
@@ -720,6 +759,27 @@ tdks_status tdks_batch_tune(tdks_batch* b, int reps, tdks_tile_choice* out, int 
   return TDKS_OK;
 }
 
+tdks_status tdks_batch_set_kb(tdks_batch* b, int sys, int n_atoms, const double* R, double a, double bb,
+                              const double c[2], int lmax) {
+  if (!b || sys < 0 || sys >= b->n_sys) return TDKS_ERR_ARG;
+  tdks_ctx* cx = b->ctx[sys];
+  B_CU(b, cudaStreamSynchronize(b->st));
+  B_TRY(b, ctx_try(b, cx, tdks_set_kb(cx, n_atoms, R, a, bb, c, lmax)), "tdks_set_kb");
+  double* part = nullptr;
+  int nblk = 0;
+  const KbView* v = kb_view(cx, &part, &nblk, nullptr);
+  if (cx->kb && !v) return bfail(b, TDKS_ERR_NOMEM, "projector view");
+  for (BSys* S : {&b->h_half[sys], &b->h_full[sys]}) {
+    S->kb = v;
+    S->kb_part = v ? part : nullptr;
+    S->kb_nblk = v ? nblk : 0;
+  }
+  invalidate_graph(b);
+  B_TRY(b, build_kb_lists(b), "projectors");
+  B_TRY(b, upload_descriptors(b), "projectors");
+  return TDKS_OK;
+}
+
 tdks_status tdks_batch_tune_kmax(tdks_batch* b, int k_cap, int64_t mem_budget, int* kmax_out) {
   if (!b || k_cap < 2 || k_cap > TDKS_KMAX) return TDKS_ERR_ARG;
   // per system, over its exponentials since creation or since its cap was last
@@ -847,11 +907,14 @@ tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]) {
     B_CU(b, cudaEventRecord(ev[0], b->st));
     B_CU(b, launch_bkry_prepare(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->st));
     B_CU(b, cudaEventRecord(ev[1], b->st));
+    B_CU(b, launch_bkb_project(sys, b->d_kb_items, b->n_kb_items, b->st));
     for (size_t i = 0; i < b->degs.size(); ++i) B_CU(b, apply_degree(b, (int)i, sys, b->st));
     B_CU(b, cudaEventRecord(ev[2], b->st));
     B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, b->st));
+    B_CU(b, launch_bkb_alpha(sys, b->d_kb_orbs, b->n_kb_orbs, b->st));
     B_CU(b, cudaEventRecord(ev[3], b->st));
     B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, b->st));
+    B_CU(b, launch_bkb_add(sys, b->d_kb_rows, b->n_kb_rows, b->st));
     B_CU(b, cudaEventRecord(ev[4], b->st));
     B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, b->st));
     B_CU(b, cudaEventRecord(ev[5], b->st));

@@ -117,26 +117,15 @@ __device__ __forceinline__ long long box_global(const KbGroup& G, int nix, int n
   return (long long)(G.I0 + i) + (long long)nix * ((G.J0 + j) + (long long)niy * (G.K0 + k));
 }
 
-// C[o][p] = sc_o sum_box Pbar_p[l] in_o[j(l)]; sc_o = s_kj of the orbital's Lanczos
-// state (0 and no work for orbitals out of the recurrence) or 1
-__global__ void k_kb_project(const KbGroup* __restrict__ grp, const int* __restrict__ pg,
-                             const double* __restrict__ vals, int nix, int niy, const double2* in,
-                             int64_t in_stride, const KryOrb* kry, int kj, double2* C, int n_proj) {
+// sc * sum_box Pbar_p[l] x[j(l)] by one block (fixed-order reduction), written by thread 0
+__device__ __forceinline__ void kb_project_block(const KbGroup* __restrict__ grp, const int* __restrict__ pg,
+                                                 const double* __restrict__ vals, int nix, int niy,
+                                                 const double2* x, double sc, int p, double2* dst) {
   __shared__ double red[2][kThreads / 32];
-  const int p = blockIdx.x, o = blockIdx.y;
-  double sc = 1.0;
-  if (kry) {
-    if (kry[o].status != KRY_ACTIVE) {
-      if (threadIdx.x == 0) C[(long long)o * n_proj + p] = make_double2(0.0, 0.0);
-      return;
-    }
-    sc = kry[o].s[kj];
-  }
   const KbGroup G = grp[pg[p]];
   const int slot = p - G.p0;
   const long long box = (long long)G.nI * G.nJ * G.nK;
   const double* v = vals + G.val_off + slot * box;
-  const double2* x = in + (long long)o * in_stride;
   double re = 0.0, im = 0.0;
   for (long long l = threadIdx.x; l < box; l += blockDim.x) {
     const double2 a = x[box_global(G, nix, niy, l)];
@@ -158,8 +147,25 @@ __global__ void k_kb_project(const KbGroup* __restrict__ grp, const int* __restr
       sr += red[0][k];
       si += red[1][k];
     }
-    C[(long long)o * n_proj + p] = make_double2(sc * sr, sc * si);
+    *dst = make_double2(sc * sr, sc * si);
   }
+}
+
+// C[o][p] = sc_o sum_box Pbar_p[l] in_o[j(l)]; sc_o = s_kj of the orbital's Lanczos
+// state (0 and no work for orbitals out of the recurrence) or 1
+__global__ void k_kb_project(const KbGroup* __restrict__ grp, const int* __restrict__ pg,
+                             const double* __restrict__ vals, int nix, int niy, const double2* in,
+                             int64_t in_stride, const KryOrb* kry, int kj, double2* C, int n_proj) {
+  const int p = blockIdx.x, o = blockIdx.y;
+  double sc = 1.0;
+  if (kry) {
+    if (kry[o].status != KRY_ACTIVE) {
+      if (threadIdx.x == 0) C[(long long)o * n_proj + p] = make_double2(0.0, 0.0);
+      return;
+    }
+    sc = kry[o].s[kj];
+  }
+  kb_project_block(grp, pg, vals, nix, niy, in + (long long)o * in_stride, sc, p, &C[(long long)o * n_proj + p]);
 }
 
 // alpha_j += sum_p |C[o][p]|^2 / h_p (after the element partials were summed)
@@ -176,21 +182,15 @@ __global__ void k_kb_alpha(KryOrb* kry, int kj, const double2* C, const double* 
   kry[o].alpha[kj] += s;
 }
 
-// out_j (+)= y_j = sum_entries sum_slots Pbar C / h over the covered nodes; in a Lanczos
-// step the partials of |w + y|^2 - |w|^2 go to part[o][block]
-__global__ void k_kb_add(const KbGroup* __restrict__ grp, const double* __restrict__ vals,
-                         const long long* __restrict__ tnode, const int* __restrict__ toff,
-                         const KbEntry* __restrict__ tent, long long n_t, const double2* C,
-                         const double* __restrict__ invh, int n_proj, double2* out,
-                         int64_t out_stride, const KryOrb* kry, double* part, int64_t part_stride) {
-  __shared__ double red[kThreads / 32];
-  const int o = blockIdx.y;
-  if (kry && kry[o].status != KRY_ACTIVE) return;
-  const double2* Co = C + (long long)o * n_proj;
-  double2* w = out + (long long)o * out_stride;
+// w_j += y_j = sum_entries sum_slots Pbar C / h over the covered nodes t = t0, t0 + dt, ...;
+// returns the sum of |w + y|^2 - |w|^2 over them
+__device__ __forceinline__ double kb_add_nodes(const KbGroup* __restrict__ grp, const double* __restrict__ vals,
+                                               const long long* __restrict__ tnode, const int* __restrict__ toff,
+                                               const KbEntry* __restrict__ tent, long long n_t, const double2* Co,
+                                               const double* __restrict__ invh, double2* w, long long t0,
+                                               long long dt) {
   double acc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_t;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = t0; t < n_t; t += dt) {
     double yr = 0.0, yi = 0.0;
     for (int e = toff[t]; e < toff[t + 1]; ++e) {
       const KbEntry E = tent[e];
@@ -205,20 +205,110 @@ __global__ void k_kb_add(const KbGroup* __restrict__ grp, const double* __restri
     }
     const long long j = tnode[t];
     double2 v = w[j];
-    if (part) acc += 2.0 * (v.x * yr + v.y * yi) + yr * yr + yi * yi;
+    acc += 2.0 * (v.x * yr + v.y * yi) + yr * yr + yi * yi;
     v.x += yr;
     v.y += yi;
     w[j] = v;
   }
-  if (!part) return;
+  return acc;
+}
+
+// block sum of acc written by thread 0 to *dst
+__device__ __forceinline__ void kb_block_sum(double acc, double* dst) {
+  __shared__ double red[kThreads / 32];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) s += red[k];
-    part[(long long)o * part_stride + blockIdx.x] = s;
+    *dst = s;
   }
+}
+
+// out_j (+)= y_j over the covered nodes; in a Lanczos step the partials of
+// |w + y|^2 - |w|^2 go to part[o][block]
+__global__ void k_kb_add(const KbGroup* __restrict__ grp, const double* __restrict__ vals,
+                         const long long* __restrict__ tnode, const int* __restrict__ toff,
+                         const KbEntry* __restrict__ tent, long long n_t, const double2* C,
+                         const double* __restrict__ invh, int n_proj, double2* out,
+                         int64_t out_stride, const KryOrb* kry, double* part, int64_t part_stride) {
+  const int o = blockIdx.y;
+  if (kry && kry[o].status != KRY_ACTIVE) return;
+  const double acc = kb_add_nodes(grp, vals, tnode, toff, tent, n_t, C + (long long)o * n_proj, invh,
+                                  out + (long long)o * out_stride,
+                                  blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                  (long long)gridDim.x * blockDim.x);
+  if (part) kb_block_sum(acc, &part[(long long)o * part_stride + blockIdx.x]);
+}
+
+}  // namespace
+
+// Device view of one context's projectors for the batched engine.
+struct KbView {
+  const KbGroup* grp;
+  const int* pg;
+  const double* vals;
+  const double* invh;
+  const long long* tnode;
+  const int* toff;
+  const KbEntry* tent;
+  double2* C;             // [n_orb][n_proj]
+  long long n_t;
+  int n_proj, n_blocks, nix, niy;
+};
+
+namespace {
+
+// the orbital's current Krylov vector V_j (j = K.k), as the batched apply reads it:
+// the exponential's start vector for j = 0 (input, or output after a sub-step),
+// the workspace otherwise
+__device__ __forceinline__ const double2* kb_bcur(const BSys& S, const KryOrb& K, int o) {
+  if (K.k == 0) return (K.nsub == 0 ? S.in : S.out) + (long long)o * S.n_int;
+  return S.Vw + ((long long)o * S.kmax + (K.k - 1)) * S.n_int;
+}
+
+__global__ void k_bkb_project(const BSys* __restrict__ sys, const BKbItem* __restrict__ items) {
+  const BKbItem it = items[blockIdx.x];
+  const BSys& S = sys[it.sys];
+  const KbView& V = *S.kb;
+  const KryOrb& K = S.kry[it.o];
+  double2* dst = &V.C[(long long)it.o * V.n_proj + it.p];
+  if (K.status != KRY_ACTIVE) {
+    if (threadIdx.x == 0) *dst = make_double2(0.0, 0.0);
+    return;
+  }
+  kb_project_block(V.grp, V.pg, V.vals, V.nix, V.niy, kb_bcur(S, K, it.o), K.s[K.k], it.p, dst);
+}
+
+__global__ void k_bkb_alpha(const BSys* __restrict__ sys, const BOrb* __restrict__ orbs, int n) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const BOrb b = orbs[g];
+  const BSys& S = sys[b.sys];
+  KryOrb& K = S.kry[b.o];
+  if (K.status != KRY_ACTIVE) return;
+  const KbView& V = *S.kb;
+  double s = 0.0;
+  for (int p = 0; p < V.n_proj; ++p) {
+    const double2 c = V.C[(long long)b.o * V.n_proj + p];
+    s = fma(V.invh[p], c.x * c.x + c.y * c.y, s);
+  }
+  K.alpha[K.k] += s;
+}
+
+// one block per (system, orbital, node block): y into the assembly's output V_{j+1}
+__global__ void k_bkb_add(const BSys* __restrict__ sys, const BRow* __restrict__ rows) {
+  const BRow r = rows[blockIdx.x];
+  const BSys& S = sys[r.sys];
+  const KryOrb& K = S.kry[r.o];
+  if (K.status != KRY_ACTIVE) return;
+  const KbView& V = *S.kb;
+  double2* w = S.Vw + ((long long)r.o * S.kmax + K.k) * S.n_int;
+  const double acc = kb_add_nodes(V.grp, V.vals, V.tnode, V.toff, V.tent, V.n_t, V.C + (long long)r.o * V.n_proj,
+                                  V.invh, w, r.rblk * (long long)blockDim.x + threadIdx.x,
+                                  (long long)S.kb_nblk * blockDim.x);
+  kb_block_sum(acc, &S.kb_part[(long long)r.o * S.kb_nblk + r.rblk]);
 }
 
 int grid_for(long long n, int cap) {
@@ -240,13 +330,15 @@ struct KbState {
   KbEntry* d_tent = nullptr;
   double2* d_C = nullptr;
   double* d_part = nullptr;     // [n_orb][n_blocks] partials of the Lanczos correction
+  KbView* d_view = nullptr;     // device view for the batched engine (made on first use)
   std::vector<double> h;
 };
 
 void kb_free(tdks_ctx* c) {
   if (!c || !c->kb) return;
   KbState* k = static_cast<KbState*>(c->kb);
-  void* ptrs[] = {k->d_grp, k->d_pg, k->d_vals, k->d_invh, k->d_tnode, k->d_toff, k->d_tent, k->d_C, k->d_part};
+  void* ptrs[] = {k->d_grp, k->d_pg, k->d_vals, k->d_invh, k->d_tnode, k->d_toff, k->d_tent, k->d_C, k->d_part,
+                  k->d_view};
   for (void* p : ptrs) cudaFree(p);
   delete k;
   c->kb = nullptr;
@@ -258,6 +350,44 @@ int kb_norm_blocks(const tdks_ctx* c) {
 }
 const double* kb_norm_parts(const tdks_ctx* c) {
   return c->kb ? static_cast<const KbState*>(c->kb)->d_part : nullptr;
+}
+
+const KbView* kb_view(tdks_ctx* c, double** part, int* n_blocks, int* n_proj) {
+  KbState* k = c ? static_cast<KbState*>(c->kb) : nullptr;
+  if (!k) return nullptr;
+  if (!k->d_view) {
+    const KbView v{k->d_grp, k->d_pg, k->d_vals, k->d_invh, k->d_tnode, k->d_toff, k->d_tent, k->d_C,
+                   k->n_t, k->n_proj, k->n_blocks, c->Ni[0], c->Ni[1]};
+    if (cudaMalloc((void**)&k->d_view, sizeof(KbView)) != cudaSuccess ||
+        cudaMemcpy(k->d_view, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(k->d_view);
+      k->d_view = nullptr;
+      return nullptr;
+    }
+  }
+  if (part) *part = k->d_part;
+  if (n_blocks) *n_blocks = k->n_t > 0 ? k->n_blocks : 0;
+  if (n_proj) *n_proj = k->n_proj;
+  return k->d_view;
+}
+
+cudaError_t launch_bkb_project(const BSys* sys, const BKbItem* items, int n_items, cudaStream_t st) {
+  if (n_items < 1) return cudaSuccess;
+  k_bkb_project<<<n_items, kThreads, 0, st>>>(sys, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkb_alpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st) {
+  if (n_orbs < 1) return cudaSuccess;
+  k_bkb_alpha<<<(n_orbs + 63) / 64, 64, 0, st>>>(sys, orbs, n_orbs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bkb_add(const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st) {
+  if (n_rows < 1) return cudaSuccess;
+  k_bkb_add<<<n_rows, kThreads, 0, st>>>(sys, rows);
+  return cudaGetLastError();
 }
 
 tdks_status kb_project(tdks_ctx* c, const ApplyArgs& a) {

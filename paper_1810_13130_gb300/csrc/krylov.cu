@@ -629,6 +629,7 @@ __global__ void k_bkry_exp(const BSys* __restrict__ sys, const BOrb* __restrict_
   const double* np = S.npart + (long long)b.o * S.n_rblk;
   double v = 0.0;
   for (int k = lane; k < S.n_rblk; k += 32) v += np[k];
+  for (int k = lane; k < S.kb_nblk; k += 32) v += S.kb_part[(long long)b.o * S.kb_nblk + k];   // nonlocal
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   const int j = K.k;
   kry_decide(K, j, S.kmax, tol, sqrt(v), W, theta);

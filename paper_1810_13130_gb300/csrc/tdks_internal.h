@@ -283,6 +283,8 @@ tdks_status ensure_part(tdks_ctx* c, int n_orb, int64_t per_orb);
 // ---------------------------------------------------------------------------
 enum { KRY_RESTART = 4 };      // ||v|| needed before the recurrence (re)starts
 
+struct KbView;                 // device view of a context's nonlocal projectors (kb.cu)
+
 struct BSys {
   Geom g;
   int P1, n_orb, kmax;
@@ -299,11 +301,16 @@ struct BSys {
   double* apart;               // alpha partials [n_orb][n_eblk]
   double* npart;               // norm partials [n_orb][n_rblk]
   double dt;
+  const KbView* kb;            // nonlocal projectors of the system, or nullptr
+  double* kb_part;             // partials of |w + y|^2 - |w|^2 of the nonlocal term [n_orb][kb_nblk]
+  int kb_nblk;                 // 0 without projectors
+  int pad1;
 };
 static_assert(sizeof(BSys) % 8 == 0, "BSys is copied as 64-bit words");
 struct BItem { int sys, eblk, o0, o1; };   // apply: E elements of block eblk, orbitals [o0, o1)
 struct BRow { int sys, o, rblk, pad; };    // one row block of one orbital
 struct BOrb { int sys, o; };               // one orbital of one system
+struct BKbItem { int sys, o, p, pad; };    // nonlocal projection: projector p of orbital o
 
 // elements.cu
 size_t hbar_batch_smem(int P1, int prec, int E);
@@ -330,6 +337,15 @@ cudaError_t launch_bloop_begin(cudaGraphConditionalHandle h, int* iter, int* qct
 cudaError_t launch_bloop_control(cudaGraphConditionalHandle h, const BSys* sys, const BOrb* orbs,
                                  int n_orbs, int* iter, int cap, int* err, int* qctr, int n_q,
                                  cudaStream_t st);
+// kb.cu, batched nonlocal term: the device view of c's projectors (nullptr without
+// them; owned by the context), its partial buffer [n_orb][*n_blocks] and projector count
+const KbView* kb_view(tdks_ctx* c, double** part, int* n_blocks, int* n_proj);
+// C of every item's (orbital, projector) from the orbital's current Krylov vector
+cudaError_t launch_bkb_project(const BSys* sys, const BKbItem* items, int n_items, cudaStream_t st);
+// alpha_j += sum_p |C_p|^2 / h_p of every listed orbital (after launch_balpha)
+cudaError_t launch_bkb_alpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st);
+// w += y over the covered nodes of block rows[i].rblk, partials to kb_part (after the assembly)
+cudaError_t launch_bkb_add(const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st);
 // sys_sub[2 s] = largest sub-step count of system s, sys_sub[2 s + 1] = its
 // orbital-vector Hbar applications (both accumulated until the host clears them)
 cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,

@@ -122,6 +122,7 @@ def lib():
         "tdks_batch_init": [v, _dp],
         "tdks_batch_tune": [v, i, p, i, C.POINTER(i)],
         "tdks_batch_tune_kmax": [v, i, i64, C.POINTER(i)],
+        "tdks_batch_set_kb": [v, i, i, _dp, d, d, _dp, i],
         "tdks_batch_steps": [v, i, _dp],
         "tdks_batch_stats": [v, C.POINTER(i64), C.POINTER(i), i],
         "tdks_batch_last_error": [v],
@@ -154,7 +155,8 @@ def exported_symbols() -> list:
                         "tdks_batch_create", "tdks_batch_destroy",
                         "tdks_batch_stream", "tdks_batch_sizes", "tdks_batch_set_orbitals",
                         "tdks_batch_get_orbitals", "tdks_batch_kick", "tdks_batch_init",
-                        "tdks_batch_tune", "tdks_batch_tune_kmax", "tdks_batch_steps", "tdks_batch_stats",
+                        "tdks_batch_tune", "tdks_batch_tune_kmax", "tdks_batch_set_kb", "tdks_batch_steps",
+                        "tdks_batch_stats",
                         "tdks_batch_last_error", "tdks_batch_set_timing", "tdks_batch_phase_ms",
                         "tdks_batch_profile_pass",
                         "tdks_last_error", "tdks_status_string")]
@@ -639,6 +641,14 @@ class Batch:
                     "tdks_batch_tune")
         return [{"p": t.p, "n_orb": t.n_orb, "elems_per_cta": t.elems_per_cta,
                  "orbs_per_item": t.orbs_per_item, "ms": t.ms} for t in out[:n.value]]
+
+    def set_kb(self, k: int, R, a: float = 1.0, b: float = 0.8, c=(-2.0, -1.0), lmax: int = 1):
+        """Kleinman-Bylander projectors on the atoms at R ([n_atoms, 3]) for system k of
+        the batch (as Context.set_kb); R empty removes them."""
+        Rh = _darr(R).reshape(-1)
+        ch = _darr(c).reshape(2)
+        self._check(lib().tdks_batch_set_kb(self.h, k, len(Rh) // 3, _ptr(Rh) if len(Rh) else None, a, b,
+                                            _ptr(ch), lmax), "tdks_batch_set_kb")
 
     def tune_kmax(self, k_cap: int = 128, mem_budget: int = -1) -> list:
         """Per-system Krylov caps after a step: k_cap for the systems whose last

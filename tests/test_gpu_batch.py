@@ -206,3 +206,52 @@ def test_batch_krylov_caps_follow_the_substeps():
         ctxs[k].close()
     with pytest.raises(tdks.TDKSError):
         b.tune_kmax(200)
+
+
+KB_ATOMS = {0: np.array([[0.3, -0.2, 0.1], [-2.1, 1.4, 0.9]]), 2: np.array([[0.3, -0.2, 0.1]])}
+
+
+@pytest.mark.parametrize("prec_name,bound", [("fp64", 1e-10), ("df64", 1e-10), ("mixed", 1e-6)])
+def test_batch_nonlocal_term_matches_oracle(prec_name, bound):
+    """tdks_batch_set_kb on two systems of a batch (Eq. 6 in Galerkin and Loewdin form;
+    one of them with three orbitals, so that each orbital projects its own Krylov
+    vector): the batched steps equal the oracle's Magnus steps with the same
+    projectors, and the systems without projectors stay as they were."""
+    from paper_1810_13130_gb300 import tdks
+    from oracle.kb import KleinmanBylander
+    prec = {"fp64": tdks.FP64, "df64": tdks.DF64, "mixed": tdks.MIXED}[prec_name]
+    cfgs = synth.small_batch()[:4]
+    psi0 = _initial(cfgs)
+    kp = synth.KBParams()
+    b, _ = _batch(cfgs, psi0, prec=prec)
+    for k, R in KB_ATOMS.items():
+        b.set_kb(k, R, kp.a, kp.b, kp.c, kp.lmax)
+    plain, _ = _batch(cfgs, psi0, prec=prec)
+    n = 2
+    dips, dplain = b.steps(n), plain.steps(n)
+    for k, c in enumerate(cfgs):
+        m = Mesh.from_config(c)
+        nl = KleinmanBylander(m, KB_ATOMS[k], kp.a, kp.b, kp.c, lmax=kp.lmax) if k in KB_ATOMS else None
+        prop = Propagator.from_config(c, m, nl=nl)
+        ref = kick(m, psi0[k], c.kick, c.kick_dir)
+        prop.init(ref)
+        for s in range(n):
+            ref, dref, _ = prop.magnus_step(ref, c.dt)
+            np.testing.assert_allclose(dips[s, k], dref, rtol=1e-8 if bound > 1e-10 else 1e-9, atol=1e-12)
+        got = b.get_orbitals(k).cpu().numpy()
+        assert _rel(got, ref) < bound
+        if k in KB_ATOMS:
+            assert _rel(got, plain.get_orbitals(k).cpu().numpy()) > 1e-4   # the term acts
+        else:
+            np.testing.assert_array_equal(dips[:, k], dplain[:, k])
+
+
+def test_batch_nonlocal_term_can_be_removed():
+    cfgs = synth.small_batch()[:3]
+    psi0 = _initial(cfgs)
+    kp = synth.KBParams()
+    a, _ = _batch(cfgs, psi0)
+    b, _ = _batch(cfgs, psi0)
+    b.set_kb(0, KB_ATOMS[0], kp.a, kp.b, kp.c, kp.lmax)
+    b.set_kb(0, np.zeros((0, 3)))
+    np.testing.assert_array_equal(b.steps(2), a.steps(2))
