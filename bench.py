@@ -12,6 +12,7 @@ Krylov tolerance 1e-10.  Metric: orbital-steps/s (value) and H-psi GDoF/s.
   python bench.py --horizon 500           # the molecule's full 500 steps per precision
   python bench.py --apply-only --prec df64  # standalone Hbar applications
   python bench.py --stage-only            # one contraction stage: CUDA cores vs tensor cores
+  python bench.py --stage-study           # dipole error with single element-kernel stages in FP32
 
 Inputs are synthetic and resident in HBM before the timed region; the working
 set (Krylov basis, 16 x 64 x 857k complex128 = 14 GB) is far larger than L2.
@@ -78,6 +79,9 @@ def parse():
                          "kernel nodes of graphs with conditional nodes; the kernels are the same)")
     ap.add_argument("--stage-only", action="store_true",
                     help="time the contraction-stage probe (CUDA cores vs tensor cores) only")
+    ap.add_argument("--stage-study", action="store_true",
+                    help="dipole error vs the oracle series with single stages of the double-float "
+                         "element kernel in FP32 (which stages need compensation)")
     ap.add_argument("--apply-only", action="store_true",
                     help="time standalone Hbar applications (16 orbitals) instead of steps")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -409,7 +413,7 @@ def _run_steps(tdks, torch, cfg, prec, steps, warmup, local_rank, psi0, dist=Non
 GOLDEN_WORKLOADS = ("config1", "config_mid")
 
 
-def _golden_dipoles(tdks, torch, cfg, prec, tile=0):
+def _golden_dipoles(tdks, torch, cfg, prec, tile=0, f32_stages=0):
     """The CUDA path over a committed oracle dipole series (tests/golden): the same
     ground state, kick, steps and tolerances.  Returns (dipoles, oracle dipoles)."""
     import numpy as np
@@ -419,6 +423,8 @@ def _golden_dipoles(tdks, torch, cfg, prec, tile=0):
     ctx.set_cg(float(s["cg_tol"]))
     if tile:
         ctx.set_apply_tile(tile)
+    if f32_stages:
+        ctx.set_f32_stages(f32_stages)
     g = torch.from_numpy(gs["psibar"].astype(complex)).cuda()
     ctx.kick(g, float(s["kappa"]), tuple(s["kick_dir"]))
     d = [ctx.init_propagation(g)]
@@ -448,6 +454,38 @@ def err_vs_oracle(tdks, torch, prec) -> dict:
         out[cfg.name] = dipole_err(d, ref)
     out["max"] = max(out.values())
     return out
+
+
+STAGE_NAMES = ("interp z", "interp y", "interp x", "kinetic x", "kinetic y", "kinetic z",
+               "interp^T z", "interp^T y", "interp^T x", "pointwise V + kinetic", "gathered input",
+               "element results")
+
+
+def stage_study(tdks, torch) -> dict:
+    """Dipole error against the oracle series (atom 100 steps, 8-orbital molecule 50
+    steps) of the double-float step with one stage, or one group of stages, of the
+    element kernel in FP32 arithmetic (tdks_set_f32_stages), beside plain DF64 and the
+    FP32 kernel."""
+    import synth
+    cases = [("none (DF64)", 0)] + [(n, 1 << i) for i, n in enumerate(STAGE_NAMES)]
+    cases += [("interp (forward)", 0x7), ("kinetic", 0x38), ("interp^T", 0x1c0),
+              ("interp, both directions", 0x1c7), ("all contractions", 0x1ff), ("all", 0xfff)]
+    rows = []
+    for label, mask in cases:
+        row = {"stages_fp32": label, "mask": mask}
+        for name in GOLDEN_WORKLOADS:
+            cfg = getattr(synth, name)()
+            d, ref = _golden_dipoles(tdks, torch, cfg, tdks.DF64, tile=8 if cfg.n_orb > 1 else 0,
+                                     f32_stages=mask)
+            row[cfg.name] = float(f"{dipole_err(d, ref):.3g}")
+        rows.append(row)
+    row = {"stages_fp32": "FP32 kernel (TDKS_FP32)", "mask": None}
+    for name in GOLDEN_WORKLOADS:
+        cfg = getattr(synth, name)()
+        d, ref = _golden_dipoles(tdks, torch, cfg, tdks.FP32, tile=8 if cfg.n_orb > 1 else 0)
+        row[cfg.name] = float(f"{dipole_err(d, ref):.3g}")
+    rows.append(row)
+    return {"mode": "stage_study", "bound": 1e-6, "rows": rows}
 
 
 def batched_err_vs_oracle(tdks, torch, prec) -> dict:
@@ -1044,6 +1082,12 @@ def main():
         return
     if args.horizon > 0:
         horizon(args, local_rank)
+        return
+    if args.stage_study:
+        import torch
+        from paper_1810_13130_gb300 import tdks
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(stage_study(tdks, torch)), flush=True)
         return
     if args.stage_only:
         import torch

@@ -442,6 +442,22 @@ tdks_status tdks_set_mixed(tdks_ctx* ctx, double relax);
  * (at most the orbital count of the call).  Results do not depend on it. */
 tdks_status tdks_set_apply_tile(tdks_ctx* ctx, int orbs_per_cta);
 
+/* Per-stage precision study of the double-float Hbar application (diagnostics, no
+ * counterpart in the paper).  The element kernel of Eqs. 15, 21 applies the
+ * sum-factorized operator as nine one-dimensional contractions in Gauss-point space
+ * (Sec. VI.A): bits 0-2 the interpolation to the Gauss points along z, y, x; bits 3-5
+ * the kinetic contractions along x, y, z; bits 6-8 the transposed interpolation along
+ * z, y, x; bit 9 the pointwise combination of the potential and kinetic terms; bit 10
+ * the gathered, Loewdin-scaled input; bit 11 the element results handed to the
+ * assembly.  Every later double-float application of the context (TDKS_DF64 and the
+ * double-float products of TDKS_MIXED) runs the stages whose bit is set in mask in
+ * FP32 arithmetic with FP32 operator coefficients and the others in double-float, so
+ * that the error each stage contributes can be measured on its own.  mask = 0
+ * (default) restores the ordinary kernel.  Degrees p = 4 and 6 only: a double-float
+ * application at another degree with a nonzero mask fails with TDKS_ERR_ARG.
+ * mask < 2^12. */
+tdks_status tdks_set_f32_stages(tdks_ctx* ctx, unsigned mask);
+
 /* Work counters of a context (for benchmarking): kernel launches issued, Hbar
  * colour launches, element-orbital applications, and -- when timing is on --
  * the summed device time of the Hbar applications inside tdks_expm measured

@@ -542,6 +542,12 @@ tdks_status tdks_set_mixed(tdks_ctx* c, double relax) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_f32_stages(tdks_ctx* c, unsigned mask) {
+  if (!c || mask >= (1u << 12)) return TDKS_ERR_ARG;
+  c->f32_stages = mask;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_apply_tile(tdks_ctx* c, int orbs_per_cta) {
   if (!c || orbs_per_cta < 0 || orbs_per_cta > 1024) return TDKS_ERR_ARG;
   c->opc_force = orbs_per_cta;

@@ -252,7 +252,37 @@ struct SplitLayout {
 // The next orbital's input columns are prefetched into shared memory during the
 // imaginary pass (7 % faster at p = 6: the loads no longer stall the two CTAs of an SM).
 // FP32 (no gain measured) and FP64 (bound by the FP64 pipe) keep the complex lines.
-template <int P1, typename T, class OrbFn>
+// Per-stage precision study of the double-float body (diagnostics,
+// tdks_set_f32_stages): a stage whose bit is set in `mask` runs in FP32 arithmetic
+// with FP32 operator coefficients, its input rounded to FP32 and its output widened
+// back.  Bits 0-2: interpolation to the Gauss points along z, y, x; 3-5: the kinetic
+// contractions along x, y, z; 6-8: the transposed interpolation along z, y, x; 9: the
+// pointwise potential and kinetic combination; 10: the gathered, scaled input;
+// 11: the element results as stored for the assembly.
+template <int P1, typename T, bool kStudy>
+__device__ __forceinline__ void stage_apply(const T* __restrict__ t, const float* tf, const T (&in)[P1],
+                                            T (&out)[P1], unsigned mask, int bit) {
+  if constexpr (kStudy) {
+    if ((mask >> bit) & 1u) {
+      float fi[P1], fo[P1];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) fi[k] = __fadd_rn(in[k].hi, in[k].lo);
+      cs_apply<P1>(tf, fi, fo);
+#pragma unroll
+      for (int k = 0; k < P1; ++k) out[k] = Df{fo[k], 0.0f};
+      return;
+    }
+  }
+  cs_apply<P1>(t, in, out);
+}
+template <bool kStudy, typename T>
+__device__ __forceinline__ void stage_round(T& x, unsigned mask, int bit) {
+  if constexpr (kStudy) {
+    if ((mask >> bit) & 1u) x = Df{__fadd_rn(x.hi, x.lo), 0.0f};
+  }
+}
+
+template <int P1, typename T, class OrbFn, bool kStudy = false>
 __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB, const T* sBT, const T* sK,
                                                      const T* sw, T* S1, T* S2, double* red,
                                                const double* __restrict__ vks, long long eidx,
@@ -260,9 +290,11 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
                                                Cx<T>* __restrict__ ev, double* part,
                                                int64_t part_stride, long long pslot,
                                                      double2* __restrict__ pfbuf,
-                                                     long long ev_ostride = 0) {
+                                                     long long ev_ostride = 0, unsigned smask = 0,
+                                                     const float* ftab = nullptr) {
   constexpr int P2 = Cfg<P1>::P2, P3 = Cfg<P1>::P3;
   constexpr int LS = SplitLayout<P1, T>::LS, PS = SplitLayout<P1, T>::PS;
+  constexpr int CSn = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;   // folded operator size
   typedef Cx<T> V;
   const int u = threadIdx.x % P1, v = threadIdx.x / P1;
   int ex = 0, ey = 0, ez = 0;
@@ -352,11 +384,12 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
             col[c] = d2f_bits(x) * (gsc[c] * scT);
           } else {
             col[c] = df_mul(d2df_bits(x), df_mul(gsc[c], scT));
+            stage_round<kStudy>(col[c], smask, 10);
           }
         }
       }
       // forward z, y, x
-      cs_apply<P1>(sB, col, t);
+      stage_apply<P1, T, kStudy>(sB, ftab, col, t, smask, 0);
       store_line(t, S1 + v * LS + u, PS);
       __syncthreads();
       // the buffer was last read before this barrier: refill it for the next orbital
@@ -368,54 +401,60 @@ __device__ __forceinline__ void hbar_elem_body_split(const Geom& g, const T* sB,
         if (on < o_end) issue(in_n);
       }
       load_line(col, S1 + v * PS + u, LS);
-      cs_apply<P1>(sB, col, t);
+      stage_apply<P1, T, kStudy>(sB, ftab, col, t, smask, 1);
       store_line(t, S2 + v * PS + u, LS);
       __syncthreads();
       T uq[P1];
       load_line(col, S2 + v * PS + u * LS, 1);
-      cs_apply<P1>(sB, col, uq);
+      stage_apply<P1, T, kStudy>(sB, ftab, col, uq, smask, 2);
       store_line(uq, S1 + v * PS + u * LS, 1);          // U (Gauss-point values)
-      cs_apply<P1>(sK, uq, t);
+      stage_apply<P1, T, kStudy>(sK, ftab ? ftab + 2 * CSn : nullptr, uq, t, smask, 3);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
         T r = vscale(vx[q], uq[q]);
         madd(r, fx, t[q]);
+        stage_round<kStudy>(r, smask, 9);
         t[q] = r;
       }
       store_line(t, S2 + v * PS + u * LS, 1);           // R
       __syncthreads();
       load_line(col, S1 + v * PS + u, LS);
-      cs_apply<P1>(sK, col, t);
+      stage_apply<P1, T, kStudy>(sK, ftab ? ftab + 2 * CSn : nullptr, col, t, smask, 4);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
         T r = S2[v * PS + q * LS + u];
         madd(r, fy, t[q]);
+        stage_round<kStudy>(r, smask, 9);
         S2[v * PS + q * LS + u] = r;
       }
       __syncthreads();
       load_line(col, S1 + v * LS + u, PS);
-      cs_apply<P1>(sK, col, t);
+      stage_apply<P1, T, kStudy>(sK, ftab ? ftab + 2 * CSn : nullptr, col, t, smask, 5);
 #pragma unroll
       for (int q = 0; q < P1; ++q) {
         T r = S2[q * PS + v * LS + u];
         madd(r, fz, t[q]);
+        stage_round<kStudy>(r, smask, 9);
         uq[q] = r;
         dot_acc(apt, col[q], r);
       }
       __syncthreads();
       // backward z, y, x
-      cs_apply<P1>(sBT, uq, t);
+      stage_apply<P1, T, kStudy>(sBT, ftab ? ftab + CSn : nullptr, uq, t, smask, 6);
       store_line(t, S1 + v * LS + u, PS);
       __syncthreads();
       load_line(col, S1 + v * PS + u, LS);
-      cs_apply<P1>(sBT, col, t);
+      stage_apply<P1, T, kStudy>(sBT, ftab ? ftab + CSn : nullptr, col, t, smask, 7);
       store_line(t, S2 + v * PS + u, LS);
       __syncthreads();
       load_line(col, S2 + v * PS + u * LS, 1);
-      cs_apply<P1>(sBT, col, t);
+      stage_apply<P1, T, kStudy>(sBT, ftab ? ftab + CSn : nullptr, col, t, smask, 8);
       if (valid) {
 #pragma unroll
-        for (int a2 = 0; a2 < P1; ++a2) evr[2 * a2 + comp] = t[a2];
+        for (int a2 = 0; a2 < P1; ++a2) {
+          stage_round<kStudy>(t[a2], smask, 11);
+          evr[2 * a2 + comp] = t[a2];
+        }
       }
       __syncthreads();
     }
@@ -478,10 +517,11 @@ template <int P1, typename T>
 struct SplitOcc {
   static constexpr int value = std::is_same<T, float>::value ? (P1 >= 8 ? 3 : 4) : 2;
 };
-template <int P1, typename T>
+template <int P1, typename T, bool kStudy = false>
 __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom g, const T* __restrict__ tab,
                                               const double* __restrict__ vks, ApplyArgs a,
-                                              int orb_per_cta, Cx<T>* __restrict__ ev) {
+                                              int orb_per_cta, Cx<T>* __restrict__ ev,
+                                              unsigned smask) {
   constexpr int P3 = Cfg<P1>::P3;
   constexpr int CS = 2 * (P1 / 2) * (P1 / 2) + 2 * (P1 / 2) + 1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -498,6 +538,13 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom
   for (int i = tid; i < 3 * CS; i += nthr) sB[i] = tab[tab_off_csB(P1) + i];
   for (int i = tid; i < P1; i += nthr) sw[i] = tab[tab_off_w(P1) + i];
   __syncthreads();
+  const float* ftab = nullptr;
+  if constexpr (kStudy) {   // FP32 copies of the folded operators for the stage study
+    __shared__ float fst[3 * CS];
+    for (int i = tid; i < 3 * CS; i += nthr) fst[i] = __fadd_rn(sB[i].hi, sB[i].lo);
+    __syncthreads();
+    ftab = fst;
+  }
   const long long eidx = (long long)blockIdx.x * blockDim.y + threadIdx.y;
   const int o0 = blockIdx.y * orb_per_cta;
   const int o1 = min(o0 + orb_per_cta, a.n_orb);
@@ -514,9 +561,10 @@ __global__ void __launch_bounds__(256, SplitOcc<P1, T>::value) k_hbar_split(Geom
     for (int o = o0; o < o1 && !any; ++o) any = a.kry[o].status == KRY_ACTIVE;
     if (!any) return;
   }
-  hbar_elem_body_split<P1, T>(g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part,
-                              a.part_stride, blockIdx.x,
-                              reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * SplitLayout<P1, T>::ES * sizeof(T))));
+  hbar_elem_body_split<P1, T, decltype(orb), kStudy>(
+      g, sB, sBT, sK, sw, S1, S2, red, vks, eidx, o0, o1, orb, ev, a.part, a.part_stride, blockIdx.x,
+      reinterpret_cast<double2*>(smem + pf_offset(off + (size_t)blockDim.y * SplitLayout<P1, T>::ES * sizeof(T))),
+      0, smask, ftab);
 }
 
 // alpha_j = sum of the element partials (fixed order), for the active orbitals
@@ -1534,8 +1582,17 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
   const size_t lines_end = (((3 * CS + P1) * sizeof(T) + 15) & ~size_t(15)) + (size_t)E * elem;
   const size_t smem = kSplit ? pf_offset(lines_end) + (size_t)E * P2 * P1 * sizeof(double2)   // + prefetch buffer
                              : lines_end;
+  // stage study (tdks_set_f32_stages): double-float applies at p = 4 and 6 only
+  constexpr bool kStudyOk = std::is_same<T, Df>::value && (P1 == 5 || P1 == 7);
+  const bool study = std::is_same<T, Df>::value && c->f32_stages != 0u;
+  if (study && !kStudyOk)
+    return tdks_fail(c, TDKS_ERR_ARG, "the per-stage precision study covers double-float applies at p = 4 and 6");
   if constexpr (kSplit) {
     TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (kStudyOk)
+      if (study)
+        TDKS_CU(c, cudaFuncSetAttribute(k_hbar_split<P1, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
   } else {
     TDKS_CU(c, set_smem(k_hbar<P1, T, kBF>, smem));
   }
@@ -1563,8 +1620,14 @@ tdks_status hbar_t(tdks_ctx* c, const ApplyArgs& a) {
                                                  : (const T*)c->d_tabdf;
   const Geom g = tdks_geom(c);
   if (c->kb) TDKS_TRY(kb_project(c, a));
-  if constexpr (kSplit)
-    k_hbar_split<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
+  if constexpr (kStudyOk) {
+    if (study)
+      k_hbar_split<P1, T, true><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev,
+                                                                                     c->f32_stages);
+    else
+      k_hbar_split<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev, 0u);
+  } else if constexpr (kSplit)
+    k_hbar_split<P1, T><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev, 0u);
   else
     k_hbar<P1, T, kBF><<<dim3(bpe, ochunks), dim3(P2, E), smem, c->stream>>>(g, tab, c->d_vks, a, opc, ev);
   if (a.lanczos && a.kry && a.part) {

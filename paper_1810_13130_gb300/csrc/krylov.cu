@@ -929,6 +929,7 @@ struct KGraph {
   const void* evec = nullptr;
   const void* kb = nullptr;
   int n_orb = 0, kmax = 0, prec = 0, reorth = 0, opc = 0, timing = 0;
+  unsigned f32_stages = 0;
   int len = 0;                             // iterations captured (<= kmax)
   double tol = 0.0, relax = 0.0;
   cudaGraph_t g = nullptr;
@@ -1074,7 +1075,8 @@ static tdks_status get_loop_graph(tdks_ctx* c, KGraphCache* K, const double2* cu
   for (auto& G : K->graphs) {
     if (G.cur == cur && G.VW == VW && G.evec == c->d_evec && G.kb == c->kb && G.n_orb == n_orb &&
         G.kmax == kmax && G.len == len && G.prec == prec && G.reorth == c->lanczos_reorth && G.opc == c->opc_force &&
-        G.timing == (c->timing ? 1 : 0) && G.tol == tol && G.relax == c->mixed_relax) {
+        G.timing == (c->timing ? 1 : 0) && G.tol == tol && G.relax == c->mixed_relax &&
+        G.f32_stages == c->f32_stages) {
       *out = &G;
       return TDKS_OK;
     }
@@ -1096,6 +1098,7 @@ static tdks_status get_loop_graph(tdks_ctx* c, KGraphCache* K, const double2* cu
   G.timing = c->timing ? 1 : 0;
   G.tol = tol;
   G.relax = c->mixed_relax;
+  G.f32_stages = c->f32_stages;
   const tdks_status st = capture_loop(c, K, G, kry, VW, wsorb, n, nb, nasm);
   if (st != TDKS_OK) {
     if (G.exec) cudaGraphExecDestroy(G.exec);

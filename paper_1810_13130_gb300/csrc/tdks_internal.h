@@ -122,6 +122,7 @@ struct tdks_ctx {
   int device_loop = 1;          // Lanczos iterations of a sub-step as one CUDA graph (krylov.cu)
   void* kgraph = nullptr;       // its cached graphs
   double mixed_relax = 1e8;     // TDKS_MIXED: FP32 contractions once every estimate <= relax * tol
+  unsigned f32_stages = 0;      // per-stage precision study of the double-float apply (diagnostics)
   double2* d_ro_part = nullptr; // its partial dots [n_orb][TDKS_KMAX][chunks]
   double2* d_ro_h = nullptr;    // its projections [n_orb][TDKS_KMAX]
   // counters

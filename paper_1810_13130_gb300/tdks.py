@@ -105,6 +105,7 @@ def lib():
         "tdks_set_kb": [v, i, _dp, d, d, _dp, i],
         "tdks_set_lanczos": [v, i],
         "tdks_set_apply_tile": [v, i],
+        "tdks_set_f32_stages": [v, C.c_uint],
         "tdks_set_mixed": [v, d],
         "tdks_set_device_loop": [v, i],
         "tdks_magnus_step_sc": [v, p, i, d, _dp, d, i, i, d, i, C.POINTER(Stats), C.POINTER(i)],
@@ -149,7 +150,7 @@ def exported_symbols() -> list:
                         "tdks_fma_probe", "tdks_contraction_probe",
                         "tdks_dipole_noalloc", "tdks_objective_forward",
                         "tdks_objective_backward", "tdks_set_kb", "tdks_kb_info", "tdks_set_lanczos",
-                        "tdks_set_apply_tile", "tdks_set_mixed", "tdks_set_device_loop",
+                        "tdks_set_apply_tile", "tdks_set_f32_stages", "tdks_set_mixed", "tdks_set_device_loop",
                         "tdks_magnus_step_sc", "tdks_spectrum", "tdks_apply_H_gll",
                         "tdks_nuclear_potential_nodes",
                         "tdks_batch_create", "tdks_batch_destroy",
@@ -304,6 +305,10 @@ class Context:
     def set_apply_tile(self, orbs_per_cta: int):
         """tdks_set_apply_tile: orbitals per CTA of the element kernel (0: automatic)."""
         self._check(lib().tdks_set_apply_tile(self.h, int(orbs_per_cta)), "tdks_set_apply_tile")
+
+    def set_f32_stages(self, mask: int):
+        """tdks_set_f32_stages: stages of the double-float apply run in FP32 (study; 0: none)."""
+        self._check(lib().tdks_set_f32_stages(self.h, int(mask)), "tdks_set_f32_stages")
 
     def get_counters(self, reset: bool = False) -> dict:
         c = Counters()
