@@ -163,7 +163,7 @@ tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int
   const size_t nf = (size_t)(c->n_elem * c->nq3);
   TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec == TDKS_MIXED ? TDKS_DF64 : prec));
   if (c->hartree) {
-    TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters));
+    TDKS_TRY(run_hartree(c, c->d_rho, c->d_vh, cg_iters, prec == TDKS_DF64 || prec == TDKS_MIXED));
   } else {
     TDKS_CU(c, cudaMemsetAsync(c->d_vh, 0, nf * sizeof(double), c->stream));
     if (cg_iters) *cg_iters = 0;
@@ -184,7 +184,7 @@ tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, 
   const size_t nf = (size_t)(c->n_elem * c->nq3);
   TDKS_TRY(launch_density(c, psi, n_orb, c->d_rho, prec));
   if (c->hartree) {
-    TDKS_TRY(hartree_graph(c, c->d_rho, c->d_vh, n_iter, err));
+    TDKS_TRY(hartree_graph(c, c->d_rho, c->d_vh, n_iter, err, prec == TDKS_DF64 || prec == TDKS_MIXED));
   } else {
     TDKS_CU(c, cudaMemsetAsync(c->d_vh, 0, nf * sizeof(double), c->stream));
   }

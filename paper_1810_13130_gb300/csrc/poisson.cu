@@ -6,9 +6,10 @@
 // stopping at ||r|| <= tol ||b||.  Preconditioners:
 //   * fast diagonalization (default): the stiffness of an axis-aligned tensor
 //     mesh is separable (see fdm.cpp), so K^-1 = S D^-1 S^T with S = Sx (x) Sy (x) Sz,
-//     applied as six strided FP64 matrix products along the three axes and a
-//     diagonal scaling; for these meshes it is the exact inverse up to rounding and
-//     CG stops after one or two iterations;
+//     applied as six strided matrix products along the three axes and a diagonal
+//     scaling; for these meshes it is the exact inverse up to rounding and CG stops
+//     after one or two iterations.  The products are FP64, or double-float for the
+//     double-float runs (a preconditioner exact to ~1e-14; the CG stays FP64);
 //   * Jacobi (diagonal of K from 1-D sums).
 // Convergence is decided on the device: once converged every later kernel of the
 // iteration returns at once, and the host polls the flag after iterations
@@ -16,7 +17,10 @@
 #include <cmath>
 #include <vector>
 
+#include "df64.cuh"
 #include "tdks_internal.h"
+
+using tdks::Df;
 
 namespace {
 
@@ -272,6 +276,99 @@ __global__ void __launch_bounds__(256) k_gemm(Gemm g, const CgState* cg) {
   }
 }
 
+// The same product in double-float arithmetic on the FP32 pipe (FP64 in and out):
+// operands split into float pairs on the integer pipe, every output an accumulator
+// (hi, err) -- hi grows by exact two-sums, the product tails and rounding errors of
+// the sums collect in err -- renormalized once at the end.  Relative error ~1e-14:
+// used for the preconditioner of the double-float runs, whose CG stays FP64.
+__device__ __forceinline__ void gemm_dfa(float& hi, float& err, Df a, Df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  err = __fadd_rn(err, __fadd_rn(e, pe));
+  hi = s;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_df(Gemm g, const CgState* cg) {
+  if (cg && cg->done) return;
+  __shared__ Df As[GK][GT + 1];
+  __shared__ Df Bs[GK][GT + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const long long b = blockIdx.z;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const double* A = g.A + b * g.sAb;
+  const double* B = g.B + b * g.sBb;
+  float hi[4][4], er[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      hi[i][j] = 0.0f;
+      er[i][j] = 0.0f;
+    }
+  const bool a_k_fast = (g.sAk == 1);
+  const bool b_n_fast = (g.sBn == 1);
+  for (int k0 = 0; k0 < g.K; k0 += GK) {
+#pragma unroll
+    for (int r = 0; r < (GT * GK) / 256; ++r) {
+      const int e = tid + 256 * r;
+      int kk, mm;
+      if (a_k_fast) {
+        kk = e % GK;
+        mm = e / GK;
+      } else {
+        mm = e % GT;
+        kk = e / GT;
+      }
+      const long long gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = tdks::d2df_bits((gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : 0.0);
+      int nn, kb;
+      if (b_n_fast) {
+        nn = e % GT;
+        kb = e / GT;
+      } else {
+        kb = e % GK;
+        nn = e / GK;
+      }
+      const long long gn = n0 + nn, gk2 = k0 + kb;
+      Bs[kb][nn] = tdks::d2df_bits((gn < g.N && gk2 < g.K) ? B[gk2 * g.sBk + gn * g.sBn] : 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      Df a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gemm_dfa(hi[i][j], er[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+  double* C = g.C + b * g.sCb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long gm = m0 + ty * 4 + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long gn = n0 + tx * 4 + j;
+      if (gn < g.N) {
+        const Df r = tdks::df_norm(hi[i][j], er[i][j]);
+        C[gm * g.sCm + gn * g.sCn] = (double)r.hi + (double)r.lo;
+      }
+    }
+  }
+}
+
 // t[i,j,k] /= lx[i] + ly[j] + lz[k]
 __global__ void k_fdm_scale(long long n, int nix, int niy, const double* lx, const double* ly,
                             const double* lz, double* t, const CgState* cg) {
@@ -293,7 +390,7 @@ int grid_for(long long n) {
 // out = transform of `in` along `axis` with S (n_a x n_a, row-major [i][mode]):
 // forward out[.., mode, ..] = sum_i S[i][mode] in[.., i, ..]; backward uses S^T.
 void axis_gemm(tdks_ctx* c, int axis, bool forward, const double* in, double* out,
-               const CgState* cg) {
+               const CgState* cg, bool df) {
   const long long nx = c->Ni[0], ny = c->Ni[1], nz = c->Ni[2];
   const double* S = c->d_fdmS[axis];
   const long long na = c->Ni[axis];
@@ -354,7 +451,10 @@ void axis_gemm(tdks_ctx* c, int axis, bool forward, const double* in, double* ou
     g.K = (int)nz;
     grid = dim3((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, 1);
   }
-  k_gemm<<<grid, 256, 0, c->stream>>>(g, cg);
+  if (df)
+    k_gemm_df<<<grid, 256, 0, c->stream>>>(g, cg);
+  else
+    k_gemm<<<grid, 256, 0, c->stream>>>(g, cg);
 }
 
 // z = S D^-1 S^T r  (exact inverse of the separable stiffness)
@@ -372,16 +472,16 @@ __global__ void k_cg_graph_end(long long n, double* x, const CgState* cg, int* e
     x[i] = 0.0;
 }
 
-void fdm_apply(tdks_ctx* c, const double* r, double* z, const CgState* cg) {
+void fdm_apply(tdks_ctx* c, const double* r, double* z, const CgState* cg, bool df) {
   const long long n = c->n_int;
-  axis_gemm(c, 0, true, r, c->d_t1, cg);
-  axis_gemm(c, 1, true, c->d_t1, c->d_t2, cg);
-  axis_gemm(c, 2, true, c->d_t2, c->d_t1, cg);
+  axis_gemm(c, 0, true, r, c->d_t1, cg, df);
+  axis_gemm(c, 1, true, c->d_t1, c->d_t2, cg, df);
+  axis_gemm(c, 2, true, c->d_t2, c->d_t1, cg, df);
   k_fdm_scale<<<grid_for(n), kThreads, 0, c->stream>>>(n, c->Ni[0], c->Ni[1], c->d_fdmL[0],
                                                       c->d_fdmL[1], c->d_fdmL[2], c->d_t1, cg);
-  axis_gemm(c, 2, false, c->d_t1, c->d_t2, cg);
-  axis_gemm(c, 1, false, c->d_t2, c->d_t1, cg);
-  axis_gemm(c, 0, false, c->d_t1, z, cg);
+  axis_gemm(c, 2, false, c->d_t1, c->d_t2, cg, df);
+  axis_gemm(c, 1, false, c->d_t2, c->d_t1, cg, df);
+  axis_gemm(c, 0, false, c->d_t1, z, cg, df);
   c->n_launch += 7;
 }
 
@@ -432,7 +532,7 @@ tdks_status poisson_setup(tdks_ctx* c, const Tables1D& t) {
 }
 
 // Solve K x = b by the preconditioned CG above; x holds the initial guess.
-tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters) {
+tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters, bool df) {
   const long long n = c->n_int;
   const int nb = grid_for(n);
   const int sbpc = stiff_blocks_per_color(c);
@@ -449,7 +549,7 @@ tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters) {
   // z = P^-1 r; rz = r.z; p = z (first direction) or z + beta p
   auto precondition = [&]() {
     if (fdm) {
-      fdm_apply(c, c->d_r, c->d_z, cg);
+      fdm_apply(c, c->d_r, c->d_z, cg, df);
     } else {
       k_jacobi<<<nb, kThreads, 0, c->stream>>>(n, c->d_r, c->d_invdiag, c->d_z, cg);
       c->n_launch += 1;
@@ -494,12 +594,12 @@ tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters) {
   return TDKS_OK;
 }
 
-tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters) {
+tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters, bool df) {
   const long long n = c->n_int;
   // b = 4 pi c
   TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
   TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
-  TDKS_TRY(run_cg_solve(c, c->d_b, c->d_phi, iters));
+  TDKS_TRY(run_cg_solve(c, c->d_b, c->d_phi, iters, df));
   TDKS_TRY(launch_interp(c, c->d_phi, vh_q));
   return TDKS_OK;
 }
@@ -509,7 +609,7 @@ tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* ite
 // once after convergence, so extra iterations cost launches only.  Needs the
 // fast-diagonalization preconditioner (one or two iterations); an unconverged
 // solve sets bit 4 of *err.
-tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err) {
+tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err, bool df) {
   if (!(c->cg_precond == 0 && c->fdm_ok))
     return tdks_fail(c, TDKS_ERR_ARG, "graph CG needs the fast-diagonalization preconditioner");
   const long long n = c->n_int;
@@ -523,7 +623,7 @@ tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, 
   k_cg_init<<<nb, kThreads, 0, c->stream>>>(n, b, c->d_Ap, c->d_r, part_vec);
   k_cg_init_fin<<<1, kThreads, 0, c->stream>>>(part_vec, nb, c->cg_tol, cg);
   auto precondition = [&]() {
-    fdm_apply(c, c->d_r, c->d_z, cg);
+    fdm_apply(c, c->d_r, c->d_z, cg, df);
     k_dot_part<<<nb, kThreads, 0, c->stream>>>(n, c->d_r, c->d_z, part_vec, cg);
     k_cg_fin_rz<<<1, kThreads, 0, c->stream>>>(part_vec, nb, cg);
     k_cg_dir<<<nb, kThreads, 0, c->stream>>>(n, c->d_z, c->d_pv, cg);
@@ -543,11 +643,11 @@ tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, 
   return TDKS_OK;
 }
 
-tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err) {
+tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err, bool df) {
   const long long n = c->n_int;
   TDKS_CU(c, cudaMemsetAsync(c->d_b, 0, n * sizeof(double), c->stream));
   TDKS_TRY(launch_load_vector(c, rho_q, c->d_b, 4.0 * M_PI));
-  TDKS_TRY(cg_solve_graph(c, c->d_b, c->d_phi, n_iter, err));
+  TDKS_TRY(cg_solve_graph(c, c->d_b, c->d_phi, n_iter, err, df));
   TDKS_TRY(launch_interp(c, c->d_phi, vh_q));
   return TDKS_OK;
 }

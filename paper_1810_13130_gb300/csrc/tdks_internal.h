@@ -254,8 +254,9 @@ tdks_status launch_combine(tdks_ctx* c, double* v_out, const double* vn, double 
                            const double* h3, const double E[3]);
 
 // poisson.cu
-tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters);
-tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters);
+// df: the fast-diagonalization preconditioner in double-float (the CG stays FP64)
+tdks_status run_hartree(tdks_ctx* c, const double* rho_q, double* vh_q, int* iters, bool df = false);
+tdks_status run_cg_solve(tdks_ctx* c, const double* b, double* x, int* iters, bool df = false);
 tdks_status poisson_setup(tdks_ctx* c, const Tables1D& t);
 
 // krylov.cu
@@ -356,8 +357,9 @@ cudaError_t launch_bkry_stats(const BSys* sys, const BOrb* orbs, int n_orbs,
 tdks_status vhxc_of(tdks_ctx* c, const double2* psi, int n_orb, double* out, int* cg_iters,
                     int prec = TDKS_FP64);
 // capturable forms of the per-system field work (no host synchronization)
-tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err);
-tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err);
+tdks_status cg_solve_graph(tdks_ctx* c, const double* b, double* x, int n_iter, int* err, bool df = false);
+tdks_status hartree_graph(tdks_ctx* c, const double* rho_q, double* vh_q, int n_iter, int* err,
+                          bool df = false);
 tdks_status vhxc_graph(tdks_ctx* c, const double2* psi, int n_orb, double* out, int n_iter,
                        int* err,
                        int prec = TDKS_FP64);

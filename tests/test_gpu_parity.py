@@ -391,6 +391,9 @@ def test_magnus_step_molecule_workload_properties():
     assert st["k_full_max"] >= st["k_half_max"] > 1 and st["substeps"] == 0
     np.testing.assert_allclose(st["dipole"], d, rtol=1e-12, atol=1e-14)
     assert _rel(out[tdks.DF64][0], psi) < 1e-10
+    # the DF64 step's double-float preconditioner (exact to ~1e-14): at this CG tolerance
+    # (1e-13) the FP64 CG takes at most one more iteration than with the FP64 one
+    assert all(a <= b + 1 for a, b in zip(out[tdks.DF64][1]["cg_iters"], st["cg_iters"]))
 
 
 def test_magnus_step_with_field_small_system():
