@@ -43,6 +43,8 @@ struct Deg {
   const void* tab = nullptr;
   int grid32 = 1;                 // TDKS_MIXED: the FP32 launch over the same work list
   const void* tab32 = nullptr;
+  BRow* d_rows_asm = nullptr;     // gather items of the class's systems (larger rows first)
+  int n_rows_asm = 0;
 };
 
 }  // namespace
@@ -69,7 +71,7 @@ struct tdks_batch {
   BSys *d_half = nullptr, *d_full = nullptr;
   BOrb* d_orbs = nullptr;
   int n_gorb = 0;
-  BRow *d_rows = nullptr, *d_rows_asm = nullptr;
+  BRow* d_rows = nullptr;
   int n_rows = 0;
   // nonlocal term of the systems that have projectors: projection items, orbitals,
   // node blocks of the gather
@@ -157,8 +159,11 @@ void free_batch(tdks_batch* b) {
   for (auto* p : b->ev) cudaFree(p);
   for (auto* p : b->apart) cudaFree(p);
   for (auto* p : b->npart) cudaFree(p);
-  for (auto& d : b->degs) cudaFree(d.d_items);
-  void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_rows_asm, b->d_ctrl, b->d_qctr,
+  for (auto& d : b->degs) {
+    cudaFree(d.d_items);
+    cudaFree(d.d_rows_asm);
+  }
+  void* ptrs[] = {b->d_half, b->d_full, b->d_orbs, b->d_rows, b->d_ctrl, b->d_qctr,
                   b->d_dof, b->d_sub, b->d_dip, b->d_kb_items, b->d_kb_orbs, b->d_kb_rows};
   for (void* p : ptrs) cudaFree(p);
   for (auto* c : b->ctx) tdks_destroy(c);
@@ -294,7 +299,15 @@ tdks_status capture_body(tdks_batch* b, const BSys* sys, int* iter, cudaGraphCon
   for (int i = 0; i < nd; ++i) B_CU(b, cudaStreamWaitEvent(s, b->body_join_ev[i], 0));
   B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, s));
   B_CU(b, launch_bkb_alpha(sys, b->d_kb_orbs, b->n_kb_orbs, s));
-  B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, s));
+  // gather of each degree class on its branch (the kernel takes the degree as a constant)
+  B_CU(b, cudaEventRecord(b->body_fork_ev, s));
+  for (int i = 0; i < nd; ++i) {
+    const Deg& d = b->degs[i];
+    B_CU(b, cudaStreamWaitEvent(b->ds[i], b->body_fork_ev, 0));
+    B_CU(b, launch_bassemble(d.P1, b->prec, sys, d.d_rows_asm, d.n_rows_asm, b->ds[i]));
+    B_CU(b, cudaEventRecord(b->body_join_ev[i], b->ds[i]));
+  }
+  for (int i = 0; i < nd; ++i) B_CU(b, cudaStreamWaitEvent(s, b->body_join_ev[i], 0));
   B_CU(b, launch_bkb_add(sys, b->d_kb_rows, b->n_kb_rows, s));
   B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, s));
   B_CU(b, launch_bkry_finish(sys, b->d_orbs, b->n_gorb, b->d_rows, b->n_rows, b->prec, s));
@@ -600,7 +613,7 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   b->n_gorb = (int)orbs.size();
   b->n_rows = (int)rows.size();
   if (balloc(b, &b->d_half, n_sys) || balloc(b, &b->d_full, n_sys) || balloc(b, &b->d_orbs, orbs.size()) ||
-      balloc(b, &b->d_rows, rows.size()) || balloc(b, &b->d_rows_asm, rows.size()) ||
+      balloc(b, &b->d_rows, rows.size()) ||
       balloc(b, &b->d_ctrl, 8) || balloc(b, &b->d_qctr, 64) || balloc(b, &b->d_dof, 1) ||
       balloc(b, &b->d_sub, 2 * (size_t)n_sys) ||
       balloc(b, &b->d_dip, (size_t)b->dip_cap * n_sys * 3))
@@ -612,7 +625,14 @@ tdks_status tdks_batch_create(int n_sys, const tdks_mesh_desc* meshes, const tdk
   });
   cudaMemcpy(b->d_orbs, orbs.data(), orbs.size() * sizeof(BOrb), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(BRow), cudaMemcpyHostToDevice);
-  cudaMemcpy(b->d_rows_asm, rows_asm.data(), rows_asm.size() * sizeof(BRow), cudaMemcpyHostToDevice);
+  for (Deg& d : b->degs) {
+    std::vector<BRow> dr;
+    for (const BRow& r : rows_asm)
+      if (b->ctx[r.sys]->P1 == d.P1) dr.push_back(r);
+    d.n_rows_asm = (int)dr.size();
+    if (balloc(b, &d.d_rows_asm, dr.size())) return fail(TDKS_ERR_NOMEM);
+    cudaMemcpy(d.d_rows_asm, dr.data(), dr.size() * sizeof(BRow), cudaMemcpyHostToDevice);
+  }
   cudaMemset(b->d_ctrl, 0, 8 * sizeof(int));
   cudaMemset(b->d_qctr, 0, 64 * sizeof(int));
   cudaMemset(b->d_dof, 0, sizeof(unsigned long long));
@@ -913,7 +933,8 @@ tdks_status tdks_batch_profile_pass(tdks_batch* b, double ms[6]) {
     B_CU(b, launch_balpha(sys, b->d_orbs, b->n_gorb, b->st));
     B_CU(b, launch_bkb_alpha(sys, b->d_kb_orbs, b->n_kb_orbs, b->st));
     B_CU(b, cudaEventRecord(ev[3], b->st));
-    B_CU(b, launch_bassemble(b->prec, sys, b->d_rows_asm, b->n_rows, b->st));
+    for (const Deg& d : b->degs)
+      B_CU(b, launch_bassemble(d.P1, b->prec, sys, d.d_rows_asm, d.n_rows_asm, b->st));
     B_CU(b, launch_bkb_add(sys, b->d_kb_rows, b->n_kb_rows, b->st));
     B_CU(b, cudaEventRecord(ev[4], b->st));
     B_CU(b, launch_bkry_exp(sys, b->d_orbs, b->n_gorb, b->tol, b->theta, b->st));

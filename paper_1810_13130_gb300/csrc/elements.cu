@@ -1023,7 +1023,8 @@ __global__ void k_balpha(const BSys* __restrict__ sys, const BOrb* __restrict__ 
 }
 
 // gather assembly with the three-term update, one block per (system, orbital, row block)
-template <typename T>
+// of one degree class (the degree as a compile-time constant, as in k_assemble)
+template <int P1, typename T>
 __global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
                                                    const BRow* __restrict__ rows) {
   __shared__ double red[4];
@@ -1038,19 +1039,11 @@ __global__ void __launch_bounds__(128) k_bassemble(const BSys* __restrict__ sys,
   const double2* qj = bvec(S, K, w.o, j);
   const double2* qm = j > 0 ? bvec(S, K, w.o, j - 1) : nullptr;
   double2* out = S.Vw + ((long long)w.o * S.kmax + j) * S.n_int;
-  const Geom g = S.g;
   const Cx<T>* evo = static_cast<const Cx<T>*>(S.ev) +
-                     (long long)w.o * S.n_elem * S.P1 * S.P1 * S.P1 * batch_omul<T>();
-  double acc = 0.0;
-  switch (S.P1) {   // uniform per block
-#define TDKS_BASM(P) \
-  case P: acc = assemble_rows<P, T>(g, evo, qj, qm, out, ca, cb, 1, 0, w.rblk, S.n_rblk); break;
-    TDKS_BASM(2) TDKS_BASM(3) TDKS_BASM(4) TDKS_BASM(5) TDKS_BASM(6) TDKS_BASM(7) TDKS_BASM(8) TDKS_BASM(9)
-#undef TDKS_BASM
-    default: break;
-  }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) S.npart[(long long)w.o * S.n_rblk + w.rblk] = s;
+                     (long long)w.o * S.n_elem * (P1 * P1 * P1) * batch_omul<T>();
+  const double acc = assemble_rows<P1, T>(S.g, evo, qj, qm, out, ca, cb, 1, 0, w.rblk, S.n_rblk);
+  const double sum = block_sum(acc, red);
+  if (threadIdx.x == 0) S.npart[(long long)w.o * S.n_rblk + w.rblk] = sum;
 }
 
 // ---------------------------------------------------------------------------
@@ -1951,15 +1944,30 @@ cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st) {
-  if (n_rows <= 0) return cudaSuccess;
-  if (prec == TDKS_FP32) k_bassemble<float><<<n_rows, 128, 0, st>>>(sys, rows);
-  else if (prec == TDKS_DF64) k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
+template <int P1>
+static cudaError_t bassemble_p(int prec, const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st) {
+  if (prec == TDKS_FP32) k_bassemble<P1, float><<<n_rows, 128, 0, st>>>(sys, rows);
+  else if (prec == TDKS_DF64) k_bassemble<P1, Df><<<n_rows, 128, 0, st>>>(sys, rows);
   else if (prec == TDKS_MIXED) {   // each orbital's rows in the type of its last product
-    k_bassemble<Df><<<n_rows, 128, 0, st>>>(sys, rows);
-    k_bassemble<float><<<n_rows, 128, 0, st>>>(sys, rows);
-  } else k_bassemble<double><<<n_rows, 128, 0, st>>>(sys, rows);
+    k_bassemble<P1, Df><<<n_rows, 128, 0, st>>>(sys, rows);
+    k_bassemble<P1, float><<<n_rows, 128, 0, st>>>(sys, rows);
+  } else k_bassemble<P1, double><<<n_rows, 128, 0, st>>>(sys, rows);
   return cudaGetLastError();
+}
+
+cudaError_t launch_bassemble(int P1, int prec, const BSys* sys, const BRow* rows, int n_rows, cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  switch (P1) {
+    case 2: return bassemble_p<2>(prec, sys, rows, n_rows, st);
+    case 3: return bassemble_p<3>(prec, sys, rows, n_rows, st);
+    case 4: return bassemble_p<4>(prec, sys, rows, n_rows, st);
+    case 5: return bassemble_p<5>(prec, sys, rows, n_rows, st);
+    case 6: return bassemble_p<6>(prec, sys, rows, n_rows, st);
+    case 7: return bassemble_p<7>(prec, sys, rows, n_rows, st);
+    case 8: return bassemble_p<8>(prec, sys, rows, n_rows, st);
+    case 9: return bassemble_p<9>(prec, sys, rows, n_rows, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int P1>

@@ -321,7 +321,8 @@ cudaError_t hbar_batch_occupancy(int P1, int prec, int E, int* blocks_per_sm);
 cudaError_t launch_hbar_batch(int P1, int prec, const BSys* sys, const BItem* items, int n_items,
                               int E, int grid, const void* tab, int* qctr, cudaStream_t st);
 cudaError_t launch_balpha(const BSys* sys, const BOrb* orbs, int n_orbs, cudaStream_t st);
-cudaError_t launch_bassemble(int prec, const BSys* sys, const BRow* rows, int n_rows,
+// rows: (system, orbital, row block) items of systems of degree P1 - 1 only
+cudaError_t launch_bassemble(int P1, int prec, const BSys* sys, const BRow* rows, int n_rows,
                              cudaStream_t st);
 // krylov.cu
 cudaError_t launch_bkry_init(const BSys* sys, const BOrb* orbs, int n_orbs, double factor,
