@@ -77,6 +77,7 @@ __global__ void k_kry_init(KryOrb* kry, int n_orb, double tau) {
   K.applies = 0;
   K.pad = 0;
   K.err = INFINITY;
+  K.cv = 0;      // the small-exponential cache lives for one exponential
 }
 
 __global__ void k_norm_part(const double2* v, int64_t stride, long long n, const KryOrb* kry,
@@ -138,8 +139,13 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // y = exp(-i tau T) e_1 into W.yr/W.yi[0..m-1] (T from W.a, W.b); false if the
-// expansion would need more than kBessMax terms.  Called by a full warp.
-__device__ bool cheb_exp(int m, double tau, ChebWork& W) {
+// expansion would need more than kBessMax terms.  Called by a full warp.  With a cache
+// (the orbital's Lanczos state): an expansion on any interval holding the Gershgorin set
+// of T is valid, so the cached interval and Bessel coefficients are reused while T's
+// set lies inside it (same time); otherwise the set widened by 1/32 of its width on each
+// side becomes the new cached interval.  The cache is emptied when an exponential starts,
+// so results depend only on the exponential's own inputs.
+__device__ bool cheb_exp(int m, double tau, ChebWork& W, KryOrb* C = nullptr) {
   const int lane = threadIdx.x & 31;
   if (m == 1) {
     if (lane == 0) {
@@ -159,6 +165,15 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
   }
   lo = warp_min(lo);
   hi = warp_max(hi);
+  const bool reuse = C && C->cv && C->ctau == tau && lo >= C->clo && hi <= C->chi;
+  if (reuse) {
+    lo = C->clo;
+    hi = C->chi;
+  } else if (C) {
+    const double wd = (hi - lo) * (1.0 / 32.0);
+    lo -= wd;
+    hi += wd;
+  }
   const double c = 0.5 * (hi + lo);
   const double R = 0.5 * (hi - lo);
   double sn, cs;
@@ -172,42 +187,58 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
     __syncwarp();
     return true;
   }
-  const int N = (int)ceil(z + 14.0 * cbrt(z) + 25.0);
+  const int N = reuse ? C->cN : (int)ceil(z + 14.0 * cbrt(z) + 25.0);
   if (N > kBessMax) return false;
-  if (lane == 0) {
-    // Miller: b_{n-1} = (2n/z) b_n - b_{n+1} from n = M down to 1.  The factor is
-    // n (2/z) with n carried as a double (exact), and the overflow test reads the
-    // exponent bits, so the FP64 pipe sees two instructions per step.
-    const int M = N + 20;
-    const double two_inv_z = 2.0 * (1.0 / z);
-    double bn1 = 0.0, bn = 1e-280, nd = (double)M, Stail = 0.0;
-    for (int n = M; n >= 1; --n, nd -= 1.0) {
-      const double bm = (nd * two_inv_z) * bn - bn1;
-      const int idx = n - 1;
-      if (idx <= N) W.J[idx] = bm;
-      else if ((idx & 1) == 0) Stail += 2.0 * bm;   // even terms past N enter the sum only
-      bn1 = bn;
-      bn = bm;
-      if ((((unsigned long long)__double_as_longlong(bn) >> 52) & 0x7ffull) > 1853ull) {   // |bn| > 2^830
-        bn *= 1e-250;
-        bn1 *= 1e-250;
-        Stail *= 1e-250;
-        for (int k = idx; k <= N && k <= M; ++k) W.J[k] *= 1e-250;
+  if (reuse) {
+    for (int k = lane; k <= N; k += 32) W.J[k] = C->cJ[k];
+    __syncwarp();
+  } else {
+    if (lane == 0) {
+      // Miller: b_{n-1} = (2n/z) b_n - b_{n+1} from n = M down to 1.  The factor is
+      // n (2/z) with n carried as a double (exact), and the overflow test reads the
+      // exponent bits, so the FP64 pipe sees two instructions per step.
+      const int M = N + 20;
+      const double two_inv_z = 2.0 * (1.0 / z);
+      double bn1 = 0.0, bn = 1e-280, nd = (double)M, Stail = 0.0;
+      for (int n = M; n >= 1; --n, nd -= 1.0) {
+        const double bm = (nd * two_inv_z) * bn - bn1;
+        const int idx = n - 1;
+        if (idx <= N) W.J[idx] = bm;
+        else if ((idx & 1) == 0) Stail += 2.0 * bm;   // even terms past N enter the sum only
+        bn1 = bn;
+        bn = bm;
+        if ((((unsigned long long)__double_as_longlong(bn) >> 52) & 0x7ffull) > 1853ull) {   // |bn| > 2^830
+          bn *= 1e-250;
+          bn1 *= 1e-250;
+          Stail *= 1e-250;
+          for (int k = idx; k <= N && k <= M; ++k) W.J[k] *= 1e-250;
+        }
+      }
+      W.scal[0] = Stail;
+    }
+    __syncwarp();
+    // normalization J_0 + 2 sum_{k >= 1} J_2k = 1 (the sum in a fixed order), then J_n
+    // for n >= 1 stored doubled: the expansion uses 2 J_n
+    {
+      double sp = 0.0;
+      for (int k = 2 + 2 * lane; k <= N; k += 64) sp += W.J[k];
+      for (int off = 16; off > 0; off >>= 1) sp += __shfl_down_sync(0xffffffffu, sp, off);
+      const double S = W.J[0] + 2.0 * __shfl_sync(0xffffffffu, sp, 0) + W.scal[0];
+      const double inv = 1.0 / S;
+      __syncwarp();
+      for (int k = lane; k <= N; k += 32) W.J[k] *= (k == 0 ? inv : 2.0 * inv);
+    }
+    if (C && N <= kChebCache) {
+      __syncwarp();
+      for (int k = lane; k <= N; k += 32) C->cJ[k] = W.J[k];
+      if (lane == 0) {
+        C->clo = lo;
+        C->chi = hi;
+        C->ctau = tau;
+        C->cN = N;
+        C->cv = 1;
       }
     }
-    W.scal[0] = Stail;
-  }
-  __syncwarp();
-  // normalization J_0 + 2 sum_{k >= 1} J_2k = 1 (the sum in a fixed order), then J_n
-  // for n >= 1 stored doubled: the expansion uses 2 J_n
-  {
-    double sp = 0.0;
-    for (int k = 2 + 2 * lane; k <= N; k += 64) sp += W.J[k];
-    for (int off = 16; off > 0; off >>= 1) sp += __shfl_down_sync(0xffffffffu, sp, off);
-    const double S = W.J[0] + 2.0 * __shfl_sync(0xffffffffu, sp, 0) + W.scal[0];
-    const double inv = 1.0 / S;
-    __syncwarp();
-    for (int k = lane; k <= N; k += 32) W.J[k] *= (k == 0 ? inv : 2.0 * inv);
   }
   const double invR = 1.0 / R;
   const double two_invR = 2.0 * invR;
@@ -275,8 +306,8 @@ __device__ bool cheb_exp(int m, double tau, ChebWork& W) {
 
 // exp(-i tau T) e_1 for either sign of tau: for tau < 0 it is the complex
 // conjugate of exp(-i |tau| T) e_1 (T and e_1 are real).
-__device__ bool cheb_exp_signed(int m, double tau, ChebWork& W) {
-  const bool ok = cheb_exp(m, fabs(tau), W);
+__device__ bool cheb_exp_signed(int m, double tau, ChebWork& W, KryOrb* C = nullptr) {
+  const bool ok = cheb_exp(m, fabs(tau), W, C);
   if (ok && tau < 0.0) {
     for (int i = (threadIdx.x & 31); i < m; i += 32) W.yi[i] = -W.yi[i];
     __syncwarp();
@@ -303,7 +334,7 @@ __device__ void kry_decide(KryOrb& K, int j, int kmax, double tol, double beta, 
   if (!isfinite(beta)) {
     decision = -1;
   } else {
-    const bool ok = cheb_exp_signed(m, K.t_rem, W);
+    const bool ok = cheb_exp_signed(m, K.t_rem, W, &K);
     const double err = ok ? fabs(K.t_rem) * beta * K.nrm * hypot(W.yr[m - 1], W.yi[m - 1]) : INFINITY;
     est = err;
     if (ok && (err <= tol || beta == 0.0)) {
@@ -572,6 +603,7 @@ __global__ void k_bkry_init(const BSys* __restrict__ sys, const BOrb* __restrict
   K.pad = 0;
   K.err = INFINITY;
   K.f32 = 0;
+  K.cv = 0;      // the small-exponential cache lives for one exponential
 }
 
 // partial ||v||^2 of the (re)starting orbitals, one block per chunk of n_int / n_rblk entries

@@ -14,6 +14,8 @@
 #define TDKS_MAX_SUBSTEPS 1000
 
 // Per-orbital Lanczos state, resident in device memory.
+constexpr int kChebCache = 511;   // largest cached Chebyshev expansion order
+
 struct KryOrb {
   double nrm;                  // ||psi|| at the start of the current sub-step
   double t_rem;                // time still to propagate
@@ -32,6 +34,13 @@ struct KryOrb {
   double s[TDKS_KMAX + 1];     // basis vector j is q_j = s[j] * V_j
   double yre[TDKS_KMAX];
   double yim[TDKS_KMAX];
+  // small-exponential cache of the current exponential: the Chebyshev interval
+  // [clo, chi] and time ctau of the last expansion and its (normalized, doubled) Bessel
+  // coefficients cJ[0..cN]; valid for any later T whose Gershgorin interval lies inside
+  // [clo, chi] (cv = 0: empty)
+  double clo, chi, ctau;
+  int cN, cv;
+  double cJ[kChebCache + 1];
 };
 
 enum { KRY_ACTIVE = 0, KRY_CONVERGED = 1, KRY_SUBSTEP = 2, KRY_DONE = 3, KRY_FAILED = -1 };
