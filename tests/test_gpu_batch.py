@@ -255,3 +255,33 @@ def test_batch_nonlocal_term_can_be_removed():
     b.set_kb(0, KB_ATOMS[0], kp.a, kp.b, kp.c, kp.lmax)
     b.set_kb(0, np.zeros((0, 3)))
     np.testing.assert_array_equal(b.steps(2), a.steps(2))
+
+
+def test_batch_timing_and_profile_pass_are_diagnostics_only():
+    """tdks_batch_set_timing / phase_ms / profile_pass: the timed graph gives the same
+    steps bit for bit, the phase times and loop passes are reported, and the profile
+    pass (the half-step exponential once more, kernel group by kernel group) leaves
+    the orbitals as they were."""
+    from paper_1810_13130_gb300 import tdks
+    cfgs = synth.small_batch()[:3]
+    psi0 = _initial(cfgs)
+    a, _ = _batch(cfgs, psi0)
+    b, _ = _batch(cfgs, psi0)
+    with pytest.raises(tdks.TDKSError):
+        b.profile_pass()                             # no step yet
+    b.set_timing(True)
+    with pytest.raises(tdks.TDKSError):
+        b.phase_ms()
+    np.testing.assert_array_equal(b.steps(2), a.steps(2))
+    ph = b.phase_ms()
+    assert all(ph[k] >= 0.0 for k in ("predictor", "half_exp", "corrector_fields", "full_exp",
+                                       "history_dipole"))
+    assert ph["half_exp"] > 0.0 and ph["full_exp"] > 0.0
+    assert all(1 <= n <= 16 * 64 for n in ph["passes"])
+    before = [b.get_orbitals(k).cpu().numpy() for k in range(len(cfgs))]
+    pp = b.profile_pass()
+    assert pp["apply"] > 0.0 and all(v >= 0.0 for v in pp.values())
+    for k in range(len(cfgs)):
+        np.testing.assert_array_equal(b.get_orbitals(k).cpu().numpy(), before[k])
+    b.set_timing(False)
+    np.testing.assert_array_equal(b.steps(1), a.steps(1))
