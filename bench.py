@@ -717,7 +717,8 @@ def graded_section(tdks, torch, args, local_rank: int, dist) -> dict:
            "steps": S, "warmup": W,
            "dipole_err": "max |d_x - d_x,fp64| / max |d_x,fp64 - d_x,fp64(0)| over the timed steps"}
     ref = None
-    for name, prec in (("fp64", tdks.FP64), ("df64", tdks.DF64), ("fp32", tdks.FP32), ("bf16", tdks.BF16)):
+    for name, prec in (("fp64", tdks.FP64), ("df64", tdks.DF64), ("mixed", tdks.MIXED), ("fp32", tdks.FP32),
+                       ("bf16", tdks.BF16)):
         try:
             c, _, t, st, _, clk = _run_steps(tdks, torch, cfg, prec, S, W, local_rank, psi0, dist,
                                              timing=False)
