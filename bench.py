@@ -600,6 +600,10 @@ def ours(args, rank: int, world: int, local_rank: int):
         hin = psi.cpu().pin_memory()
         hout = torch.empty_like(hin).pin_memory()
         E = np.zeros(6)
+        # one untimed call: the first allocates the device copy of the orbitals and
+        # captures the Lanczos-loop graphs for its address
+        ctx.propagate_host(hin, hout, 1, cfg.dt, E, init=False, tol=cfg.tol, k_max=cfg.k_max, prec=prec)
+        hin, hout = hout, hin
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
