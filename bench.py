@@ -79,6 +79,10 @@ def parse():
                          "kernel nodes of graphs with conditional nodes; the kernels are the same)")
     ap.add_argument("--stage-only", action="store_true",
                     help="time the contraction-stage probe (CUDA cores vs tensor cores) only")
+    ap.add_argument("--batch-profile", action="store_true",
+                    help="the 64-system batch (--prec fp64, df64 or mixed): one half-step "
+                         "exponential re-run kernel by kernel inside the NVTX range "
+                         "batch_profile_pass (for an ncu launch list)")
     ap.add_argument("--stage-study", action="store_true",
                     help="dipole error vs the oracle series with single stages of the double-float "
                          "element kernel in FP32 (which stages need compensation)")
@@ -486,6 +490,36 @@ def stage_study(tdks, torch) -> dict:
         row[cfg.name] = float(f"{dipole_err(d, ref):.3g}")
     rows.append(row)
     return {"mode": "stage_study", "bound": 1e-6, "rows": rows}
+
+
+def batch_profile(tdks, torch, prec_name: str) -> dict:
+    """The 64-system batch after tuning, one step at k_max 64, the Krylov caps and one
+    more step (graphs, not profiled), then the half-step exponential of the current state
+    once more outside the graph, kernel group by kernel group, inside the NVTX range
+    batch_profile_pass; with the phase times of the last step (CUDA events)."""
+    import synth
+    prec = {"fp64": tdks.FP64, "df64": tdks.DF64, "mixed": tdks.MIXED}[prec_name]
+    cfgs, dts, dirs = synth.config5()
+    b = tdks.Batch(cfgs, dts, prec=prec, tol=1e-10, k_max=64)
+    for k, c in enumerate(cfgs):
+        psi = synth.smooth_orbitals(tuple((len(c.X) - 1) * c.p - 1 for _ in range(3)), c.n_orb, seed=500 + k)
+        b.set_orbitals(k, torch.from_numpy(psi).cuda())
+    b.kick([c.kick for c in cfgs], dirs)
+    b.init()
+    b.tune(reps=2)
+    b.steps(1)
+    b.tune_kmax(BATCH_KCAP)
+    b.set_timing(True)
+    b.steps(1)
+    phases = b.phase_ms()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("batch_profile_pass")
+    groups = b.profile_pass()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    b.close()
+    return {"mode": "batch_profile", "prec": prec_name, "phases_ms": phases,
+            "half_step_groups_ms": groups}
 
 
 def batched_err_vs_oracle(tdks, torch, prec) -> dict:
@@ -1087,6 +1121,12 @@ def main():
         return
     if args.horizon > 0:
         horizon(args, local_rank)
+        return
+    if args.batch_profile:
+        import torch
+        from paper_1810_13130_gb300 import tdks
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(batch_profile(tdks, torch, args.prec)), flush=True)
         return
     if args.stage_study:
         import torch
