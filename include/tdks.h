@@ -350,13 +350,16 @@ tdks_status tdks_objective_backward(tdks_ctx* ctx, int n_s, double* dJdE_host);
  *   whose larger basis cannot be allocated keeps its cap.  Writes the caps
  *   [n_sys] to kmax_out (may be NULL).  The orbitals are unchanged; later steps
  *   take at most as many sub-steps as before and reach the same tolerance.
- *   The step graph is rebuilt on the next tdks_batch_steps call.
+ *   The step graph is rebuilt on the next tdks_batch_steps call.  TDKS_ERR_ARG for
+ *   k_cap outside 2..128 or before any step.
  * tdks_batch_set_kb: the nonlocal Kleinman-Bylander term of tdks_set_kb (same
  *   arguments, same projectors and storage) for system sys of the batch; every later
  *   step of that system applies Hbar + Hbar_nl in its Lanczos iterations (projection
  *   with each orbital's own Krylov vector, alpha and the norm of the new vector
- *   corrected as in the single-system path).  n_atoms = 0 removes it.  Synchronizes;
- *   the step graph is rebuilt on the next tdks_batch_steps call.
+ *   corrected as in the single-system path; Eq. 6).  n_atoms = 0 removes it.
+ *   Synchronizes; the step graph is rebuilt on the next tdks_batch_steps call.
+ *   TDKS_ERR_ARG for sys outside 0..n_sys-1 or the argument errors of tdks_set_kb;
+ *   TDKS_ERR_NOMEM if the projector storage cannot be allocated.
  * tdks_batch_steps: n_steps steps of every system; dipoles [n_steps][n_sys][3].
  *   Synchronizes.  TDKS_ERR_NOT_CONVERGED if a Lanczos loop failed or hit its
  *   pass cap (16 x the largest k_max passes) or a Poisson solve did not converge.
